@@ -1,0 +1,82 @@
+"""The oracle pins must catch plausible mistakes: each mutant below is the oracle
+with one planted error (compiled on the CPU into a temporary library), and at
+least one pin (brute force, closed form or hand-counted toy) must reject it."""
+from __future__ import annotations
+
+import math
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle.bruteforce import brute_force
+
+from cases import complete_bidirected, golden_cases, out_star, random_case, star_q, undirected_q
+
+SRC = os.path.join(os.path.dirname(O.__file__), "oracle.c")
+
+MUTANTS = {
+    "no_injectivity": ("if (hw == v) return 0;", ""),
+    "no_reverse_edge_check":
+        ("if (!og_pair_ok(s->qedge[w][u], og_edge(g, hw, v))) return 0;", ""),
+    "non_induced": ("if (ql == OG_NOEDGE) return gl == OG_NOEDGE;",
+                    "if (ql == OG_NOEDGE) return 1;"),
+    "no_self_loop_check": ("if (!og_pair_ok(s->qedge[u][u], og_edge(g, v, v))) return 0;", ""),
+    "absent_is_a_value": [("if (va == OG_ABSENT) return 0;", ""),
+                          ("if (vb == OG_ABSENT) return 0;", "")],
+    "ignores_false": ("if (q->y_false) y_ok = 0;", ""),
+    "ignores_edge_labels": ("return og_label_ok(ql, gl);", "return 1;"),
+    "transposed_edge": ("og_pair_ok(s->qedge[u][w], og_edge(g, v, hw))",
+                        "og_pair_ok(s->qedge[u][w], og_edge(g, hw, v))"),
+    "search_off_by_one": ("if (g->out_nbr[mid] < b) lo = mid + 1;",
+                          "if (g->out_nbr[mid] <= b) lo = mid + 1;"),
+    "var_literal_wrong_attr": ("vb = og_attr(s->g, l->b, s->h[l->y]);",
+                               "vb = og_attr(s->g, l->a, s->h[l->y]);"),
+    "vertex_label_ignored": ("if (!og_label_ok(s->q->node_label[u], g->vlabel[v])) return 0;", ""),
+}
+
+
+def _pins_pass(lib) -> bool:
+    def run(g, q):
+        return O.validate(g, q, lib=lib)
+
+    for seed in range(80):
+        g, q = random_case(seed)
+        nm, v = run(g, q)
+        bnm, bv = brute_force(g, q)
+        if nm != bnm or not np.array_equal(v, bv):
+            return False
+    for n in (4, 6):
+        if run(complete_bidirected(n), undirected_q(3, [(0, 1), (1, 2), (0, 2)]))[0] != n * (n - 1) * (n - 2):
+            return False
+        if run(complete_bidirected(n), undirected_q(3, [(0, 1), (1, 2)]))[0] != 0:
+            return False
+    if run(out_star(6), star_q(3))[0] != math.perm(6, 3):
+        return False
+    for name, g, q, n_matches, viol in golden_cases():
+        nm, v = run(g, q)
+        if nm != n_matches or not np.array_equal(v, viol):
+            return False
+    return True
+
+
+def test_unmutated_oracle_passes(oracle_mod):
+    assert _pins_pass(O.bind_library(O.build_oracle()))
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, name):
+    edits = MUTANTS[name]
+    edits = edits if isinstance(edits, list) else [edits]
+    src = open(SRC).read()
+    for old, new in edits:
+        assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+        src = src.replace(old, new)
+    mpath = tmp_path / f"{name}.c"
+    mpath.write_text(src)
+    lib_path = tmp_path / f"lib{name}.so"
+    subprocess.run(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", str(lib_path), str(mpath)],
+                   check=True)
+    assert not _pins_pass(O.bind_library(str(lib_path))), f"pins did not catch {name}"
