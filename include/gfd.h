@@ -1,0 +1,194 @@
+/*
+ * gfd.h — C-ABI of the GB300 GFD validation library (libgfd.so).
+ *
+ * The calls follow the paper's statement of the validation problem (Section II,
+ * "the validation problem"): given a graph G and a set Σ of GFDs, find
+ * Vio(Σ, G), the matches h(x̄) of each φ = (Q[x̄], X → Y) that satisfy X and
+ * not Y (or satisfy X when Y is `false`). The matching itself follows
+ * Section III.B (FastGFDs): a compact path index (candidate filtering by label
+ * and degree, breadth-first refinement that removes dead ends, index edges
+ * along a spanning tree of Q, remaining edges checked afterwards) and a
+ * core-first matching order.
+ *
+ * Conventions for every call:
+ *   - Return value: GFD_OK (0) or one of the GFD_ERR_* codes. On an error,
+ *     gfd_last_error() returns a message for the calling thread and no output
+ *     pointer is written.
+ *   - Inputs are read during the call only (copied where kept); the caller keeps
+ *     ownership of everything it passes in. All input pointers are HOST pointers.
+ *   - Handles returned by the library (gfd_graph, gfd_result) are owned by the
+ *     caller and released with the matching *_free call; *_free(NULL) is a no-op.
+ *   - All GPU work is issued on opts->cuda_stream (a cudaStream_t) when given,
+ *     else on a stream owned by the graph handle. Calls are blocking: when they
+ *     return, the results they report are final.
+ *   - Every wait the library performs on the device is bounded; a wait that runs
+ *     out returns GFD_ERR_TIMEOUT instead of hanging.
+ */
+#ifndef GFD_H
+#define GFD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gfd_graph gfd_graph;    /* opaque, device-resident, library-owned */
+typedef struct gfd_result gfd_result;  /* opaque, library-owned */
+
+enum {
+    GFD_OK = 0,
+    GFD_ERR_INVALID_ARG = 1,   /* malformed graph, pattern or literal */
+    GFD_ERR_UNSUPPORTED = 2,   /* valid but outside what the library handles */
+    GFD_ERR_OUT_OF_MEMORY = 3, /* device or host allocation failed */
+    GFD_ERR_OVERFLOW = 4,      /* a bounded buffer could not hold the result */
+    GFD_ERR_TIMEOUT = 5,       /* a bounded device wait ran out */
+    GFD_ERR_CUDA = 6           /* a CUDA runtime call failed */
+};
+
+/* Label value "_" that matches any label (Section II, wildcard). */
+#define GFD_WILDCARD (-1)
+/* Attribute value meaning "vertex has no such attribute" (Section II: a literal
+ * is satisfied only when the attribute exists). */
+#define GFD_ATTR_ABSENT INT32_MIN
+/* Largest pattern handled: |V_Q| <= GFD_MAX_K. */
+#define GFD_MAX_K 16
+
+/*
+ * Graph G = (V, E, L, F_A) (Section II, "directed labeled graphs with
+ * attributes"): V = {0 .. n_vertices-1}, E ⊆ V×V a set (at most one edge per
+ * ordered pair, self-loops allowed), a label per vertex and per edge, and an
+ * int32 attribute tuple per vertex. Layout:
+ *   out_off    [n_vertices+1]  CSR row offsets, out_off[0] = 0, non-decreasing,
+ *                              out_off[n_vertices] = n_edges
+ *   out_dst    [n_edges]       destinations, strictly increasing within a row
+ *   out_elabel [n_edges]       edge labels, 0 <= label <= 255
+ *   in_off/in_src/in_elabel    the reverse CSR (rows by destination, sources
+ *                              strictly increasing); all three NULL = built by
+ *                              the library. If given, must describe the same E.
+ *   vlabel     [n_vertices]    vertex labels, 0 <= label <= 65534
+ *   attrs      [n_attrs][n_vertices]  structure of arrays; GFD_ATTR_ABSENT = none
+ * Limits: n_edges < 2^32, and n_vertices <= 2^(32 - b) where b is the number of
+ * bits of the largest edge label (at least 1); beyond them GFD_ERR_UNSUPPORTED.
+ */
+typedef struct {
+    int32_t n_vertices;
+    int64_t n_edges;
+    int32_t n_attrs;
+    const int64_t *out_off;
+    const int32_t *out_dst;
+    const int32_t *out_elabel;
+    const int64_t *in_off;
+    const int32_t *in_src;
+    const int32_t *in_elabel;
+    const int32_t *vlabel;
+    const int32_t *attrs;
+} gfd_graph_desc;
+
+/* Attribute constraint (Section II): kind 0 is the constant constraint
+ * x.A = c (fields x, a, c); kind 1 is the variable constraint x.A = y.B
+ * (fields x, a, y, b). x and y are pattern node ids, a and b attribute ids. */
+typedef struct {
+    int32_t kind;
+    int32_t x, a;
+    int32_t y, b;
+    int32_t c;
+} gfd_literal;
+
+/*
+ * GFD φ = (Q[x̄], X → Y) or (Q[x̄], X → false) (Section II). Pattern node i is
+ * the variable x_i (μ is the identity). node_label[k]: label or GFD_WILDCARD.
+ * Directed pattern edges esrc[i] -> edst[i] with label elabel[i] (or
+ * GFD_WILDCARD), at most one per ordered pair. X has nx literals, Y has ny;
+ * y_false != 0 means the right-hand side is `false` (Y is then ignored).
+ * Limits: 1 <= k <= GFD_MAX_K and Q connected, else GFD_ERR_UNSUPPORTED.
+ */
+typedef struct {
+    int32_t k;
+    const int32_t *node_label;
+    int32_t m;
+    const int32_t *esrc;
+    const int32_t *edst;
+    const int32_t *elabel;
+    int32_t nx;
+    const gfd_literal *X;
+    int32_t ny;
+    const gfd_literal *Y;
+    int32_t y_false;
+} gfd_gfd;
+
+/* gfd_opts.flags */
+#define GFD_FLAG_NO_REFINE     0x1  /* candidate filter only: skip the top-down and
+                                       bottom-up refinement (results unchanged) */
+#define GFD_FLAG_HOST_LOOP     0x2  /* drive the enumeration from a host loop of
+                                       per-step launches instead of one persistent
+                                       cooperative launch (results unchanged) */
+#define GFD_FLAG_PROFILE       0x4  /* time each kernel class with CUDA events;
+                                       read back with gfd_result_profile() */
+#define GFD_FLAG_NO_GRAPH      0x8  /* host loop without CUDA-graph capture */
+
+/* Tuning options; a NULL gfd_opts* or zero fields select the defaults. */
+typedef struct {
+    int64_t frontier_budget_bytes; /* device bytes for partial-match buffers */
+    int32_t chunk_rows;            /* partial matches expanded per step and GFD */
+    int32_t block_threads;         /* threads per block of the expansion kernel */
+    int64_t max_violations_hint;   /* initial violation capacity per GFD */
+    void *cuda_stream;             /* cudaStream_t to issue work on */
+    int32_t flags;                 /* GFD_FLAG_* */
+} gfd_opts;
+
+/* Copy a graph to the device, validate it (row order, ranges, label limits,
+ * reverse CSR consistency) and keep it resident. *out is set on GFD_OK. */
+int gfd_graph_load(const gfd_graph_desc *desc, const gfd_opts *opts, gfd_graph **out);
+
+/* Release a graph handle and its device memory. */
+void gfd_graph_free(gfd_graph *g);
+
+/* Vertex count, edge count and resident device bytes of a loaded graph. */
+int32_t gfd_graph_vertices(const gfd_graph *g);
+int64_t gfd_graph_edges(const gfd_graph *g);
+int64_t gfd_graph_device_bytes(const gfd_graph *g);
+
+/* Validate one GFD: every match of Q is enumerated and checked (Section II,
+ * Vio({φ}, G); Section III.B, the CPI and core-first matching). *out receives
+ * the result handle on GFD_OK. */
+int gfd_validate(const gfd_graph *g, const gfd_gfd *phi, const gfd_opts *opts,
+                 gfd_result **out);
+
+/* Validate n GFDs against the same resident graph in one batched run: the
+ * candidate filters are shared between GFDs and all GFDs' matches are expanded
+ * together by one persistent launch (Section II, Vio(Σ, G) as the per-GFD
+ * lists). out[i] receives the result of phis[i]; on an error no entry is set. */
+int gfd_validate_batch(const gfd_graph *g, const gfd_gfd *const *phis, int32_t n,
+                       const gfd_opts *opts, gfd_result **out);
+
+/* Number of matches of Q (all of them, whether or not they satisfy X). */
+uint64_t gfd_result_matches(const gfd_result *r);
+/* Number of violations |Vio({φ}, G)|. */
+uint64_t gfd_result_violations(const gfd_result *r);
+/* k, the length of each violation tuple. */
+int32_t gfd_result_arity(const gfd_result *r);
+/* The violations as [n_violations][k] int32 tuples (h(x_0), ..., h(x_{k-1})),
+ * sorted lexicographically; host memory owned by the result. The sort and the
+ * copy to the host happen on the first call. NULL on error (see
+ * gfd_last_error) or when there are no violations. */
+const int32_t *gfd_result_tuples(gfd_result *r);
+/* Device time in milliseconds spent in kernel class `which` (0 candidate
+ * filter, 1 refinement, 2 index build, 3 enumeration, 4 result sort) and the
+ * number of launches, when GFD_FLAG_PROFILE was set; else 0. */
+double gfd_result_profile(const gfd_result *r, int32_t which, int64_t *launches);
+/* Statistics of the run: 0 supersteps, 1 work items expanded, 2 partial
+ * matches written, 3 edge-lookup probes, 4 candidate-list entries (sum over
+ * pattern nodes), 5 index entries. */
+uint64_t gfd_result_stat(const gfd_result *r, int32_t which);
+/* Release a result. */
+void gfd_result_free(gfd_result *r);
+
+/* Message for the calling thread's last non-OK return ("" if none). */
+const char *gfd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GFD_H */

@@ -1,0 +1,293 @@
+"""Python binding of libgfd.so (include/gfd.h): GFD validation on the GPU.
+
+Argument marshalling only: every step of validation runs in the library's CUDA
+kernels. The names follow the C-ABI (graph_load, validate, validate_batch).
+If the compiled library is missing and cannot be built, importing the binding
+raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libgfd.so")
+
+GFD_OK = 0
+GFD_ERR_INVALID_ARG = 1
+GFD_ERR_UNSUPPORTED = 2
+GFD_ERR_OUT_OF_MEMORY = 3
+GFD_ERR_OVERFLOW = 4
+GFD_ERR_TIMEOUT = 5
+GFD_ERR_CUDA = 6
+WILDCARD = -1
+ATTR_ABSENT = np.iinfo(np.int32).min
+MAX_K = 16
+
+FLAG_NO_REFINE = 0x1
+FLAG_HOST_LOOP = 0x2
+FLAG_PROFILE = 0x4
+FLAG_NO_GRAPH = 0x8
+
+PROF_FILTER, PROF_REFINE, PROF_INDEX, PROF_ENUM, PROF_SORT = range(5)
+STAT_STEPS, STAT_WORK, STAT_ROWS, STAT_PROBES, STAT_CANDIDATES, STAT_INDEX = range(6)
+
+
+class GfdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"gfd error {code}: {msg}")
+        self.code = code
+
+
+class gfd_graph_desc(C.Structure):
+    _fields_ = [("n_vertices", C.c_int32), ("n_edges", C.c_int64), ("n_attrs", C.c_int32),
+                ("out_off", C.c_void_p), ("out_dst", C.c_void_p), ("out_elabel", C.c_void_p),
+                ("in_off", C.c_void_p), ("in_src", C.c_void_p), ("in_elabel", C.c_void_p),
+                ("vlabel", C.c_void_p), ("attrs", C.c_void_p)]
+
+
+class gfd_literal(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("x", C.c_int32), ("a", C.c_int32),
+                ("y", C.c_int32), ("b", C.c_int32), ("c", C.c_int32)]
+
+
+class gfd_gfd(C.Structure):
+    _fields_ = [("k", C.c_int32), ("node_label", C.c_void_p),
+                ("m", C.c_int32), ("esrc", C.c_void_p), ("edst", C.c_void_p), ("elabel", C.c_void_p),
+                ("nx", C.c_int32), ("X", C.c_void_p), ("ny", C.c_int32), ("Y", C.c_void_p),
+                ("y_false", C.c_int32)]
+
+
+class gfd_opts(C.Structure):
+    _fields_ = [("frontier_budget_bytes", C.c_int64), ("chunk_rows", C.c_int32),
+                ("block_threads", C.c_int32), ("max_violations_hint", C.c_int64),
+                ("cuda_stream", C.c_void_p), ("flags", C.c_int32)]
+
+
+# exported functions: name -> (restype, argtypes)
+_SIGS = {
+    "gfd_graph_load": (C.c_int, [C.POINTER(gfd_graph_desc), C.POINTER(gfd_opts), C.POINTER(C.c_void_p)]),
+    "gfd_graph_free": (None, [C.c_void_p]),
+    "gfd_graph_vertices": (C.c_int32, [C.c_void_p]),
+    "gfd_graph_edges": (C.c_int64, [C.c_void_p]),
+    "gfd_graph_device_bytes": (C.c_int64, [C.c_void_p]),
+    "gfd_validate": (C.c_int, [C.c_void_p, C.POINTER(gfd_gfd), C.POINTER(gfd_opts), C.POINTER(C.c_void_p)]),
+    "gfd_validate_batch": (C.c_int, [C.c_void_p, C.POINTER(C.POINTER(gfd_gfd)), C.c_int32,
+                                     C.POINTER(gfd_opts), C.POINTER(C.c_void_p)]),
+    "gfd_result_matches": (C.c_uint64, [C.c_void_p]),
+    "gfd_result_violations": (C.c_uint64, [C.c_void_p]),
+    "gfd_result_arity": (C.c_int32, [C.c_void_p]),
+    "gfd_result_tuples": (C.c_void_p, [C.c_void_p]),
+    "gfd_result_profile": (C.c_double, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
+    "gfd_result_stat": (C.c_uint64, [C.c_void_p, C.c_int32]),
+    "gfd_result_free": (None, [C.c_void_p]),
+    "gfd_last_error": (C.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libgfd.so (building it with nvcc first if it is absent)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            if not build_if_missing:
+                raise ImportError(f"{_LIB_PATH} is missing; build it with __graft_entry__.build()")
+            from . import build as _b
+            _b.build()
+        lib = C.CDLL(_LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != GFD_OK:
+        raise GfdError(rc, _lib.gfd_last_error().decode())
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _i64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None and a.size else None
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))   # torch.cuda.Stream
+
+
+def make_opts(frontier_budget_bytes=0, chunk_rows=0, block_threads=0, max_violations_hint=0,
+              stream=None, flags=0) -> gfd_opts:
+    o = gfd_opts()
+    o.frontier_budget_bytes = int(frontier_budget_bytes)
+    o.chunk_rows = int(chunk_rows)
+    o.block_threads = int(block_threads)
+    o.max_violations_hint = int(max_violations_hint)
+    o.cuda_stream = _stream_handle(stream)
+    o.flags = int(flags)
+    return o
+
+
+class _GfdBuf:
+    """ctypes image of one GFD (keeps its arrays alive)."""
+
+    def __init__(self, gfd):
+        k = len(gfd.node_label)
+        self.nl = _i32(gfd.node_label)
+        e = np.asarray(gfd.edges, dtype=np.int32).reshape(-1, 3)
+        self.es, self.ed, self.el = _i32(e[:, 0]), _i32(e[:, 1]), _i32(e[:, 2])
+
+        def lits(ls):
+            arr = (gfd_literal * max(1, len(ls)))()
+            for i, l in enumerate(ls):
+                arr[i] = gfd_literal(l.kind, l.x, l.a, l.y, l.b, l.c)
+            return arr
+        self.X = lits(gfd.X)
+        self.Y = lits(gfd.Y)
+        s = gfd_gfd()
+        s.k = k
+        s.node_label = _ptr(self.nl)
+        s.m = e.shape[0]
+        s.esrc, s.edst, s.elabel = _ptr(self.es), _ptr(self.ed), _ptr(self.el)
+        s.nx, s.X = len(gfd.X), C.cast(self.X, C.c_void_p)
+        s.ny, s.Y = len(gfd.Y), C.cast(self.Y, C.c_void_p)
+        s.y_false = 1 if gfd.y_false else 0
+        self.s = s
+
+
+class Result:
+    """Matches and violations of one GFD."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.gfd_result_free(self._h)
+            self._h = None
+
+    @property
+    def n_matches(self) -> int:
+        return int(_lib.gfd_result_matches(self._h))
+
+    @property
+    def n_violations(self) -> int:
+        return int(_lib.gfd_result_violations(self._h))
+
+    @property
+    def k(self) -> int:
+        return int(_lib.gfd_result_arity(self._h))
+
+    def violations(self) -> np.ndarray:
+        """[n_violations, k] int32, lexicographically sorted (sorted on the device)."""
+        n, k = self.n_violations, self.k
+        p = _lib.gfd_result_tuples(self._h)
+        if n == 0:
+            return np.zeros((0, k), dtype=np.int32)
+        if not p:
+            _check(GFD_ERR_CUDA)
+        buf = (C.c_int32 * (n * k)).from_address(p)
+        return np.frombuffer(buf, dtype=np.int32).reshape(n, k).copy()
+
+    def profile(self, which: int):
+        """(device milliseconds, launches) of a kernel class (needs FLAG_PROFILE)."""
+        n = C.c_int64(0)
+        ms = _lib.gfd_result_profile(self._h, int(which), C.byref(n))
+        return float(ms), int(n.value)
+
+    def stat(self, which: int) -> int:
+        return int(_lib.gfd_result_stat(self._h, int(which)))
+
+
+class Graph:
+    """A graph resident on the GPU (gfd_graph_load)."""
+
+    def __init__(self, graph, stream=None, with_reverse: bool = False):
+        lib = load_library()
+        n = int(graph.n_vertices)
+        self.n = n
+        off = _i64(graph.out_off)
+        dst = _i32(graph.out_dst)
+        lab = _i32(graph.out_elabel)
+        vl = _i32(graph.vlabel)
+        at = _i32(graph.attrs).reshape(-1)
+        d = gfd_graph_desc()
+        d.n_vertices = n
+        d.n_edges = int(dst.shape[0])
+        d.n_attrs = int(np.asarray(graph.attrs).shape[0]) if n else int(np.asarray(graph.attrs).shape[0])
+        d.out_off, d.out_dst, d.out_elabel = _ptr(off), _ptr(dst), _ptr(lab)
+        keep = [off, dst, lab, vl, at]
+        if with_reverse:
+            src = np.repeat(np.arange(n, dtype=np.int64), np.diff(off))
+            order = np.lexsort((src, dst))
+            ioff = np.zeros(n + 1, dtype=np.int64)
+            np.cumsum(np.bincount(dst, minlength=n), out=ioff[1:])
+            isrc, ilab = _i32(src[order]), _i32(lab[order])
+            keep += [ioff, isrc, ilab]
+            d.in_off, d.in_src, d.in_elabel = _ptr(ioff), _ptr(isrc), _ptr(ilab)
+        d.vlabel, d.attrs = _ptr(vl), _ptr(at)
+        o = make_opts(stream=stream)
+        h = C.c_void_p(None)
+        _check(lib.gfd_graph_load(C.byref(d), C.byref(o), C.byref(h)))
+        del keep
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.gfd_graph_free(self._h)
+            self._h = None
+
+    @property
+    def device_bytes(self) -> int:
+        return int(_lib.gfd_graph_device_bytes(self._h))
+
+    def validate(self, gfd, **opts) -> Result:
+        o = make_opts(**opts)
+        b = _GfdBuf(gfd)
+        h = C.c_void_p(None)
+        _check(_lib.gfd_validate(self._h, C.byref(b.s), C.byref(o), C.byref(h)))
+        return Result(h)
+
+    def validate_batch(self, gfds, **opts) -> list:
+        o = make_opts(**opts)
+        bufs = [_GfdBuf(g) for g in gfds]
+        arr = (C.POINTER(gfd_gfd) * max(1, len(bufs)))(*[C.pointer(b.s) for b in bufs])
+        outs = (C.c_void_p * max(1, len(bufs)))()
+        _check(_lib.gfd_validate_batch(self._h, arr, len(bufs), C.byref(o), outs))
+        return [Result(C.c_void_p(outs[i])) for i in range(len(bufs))]
+
+
+def graph_load(graph, stream=None, with_reverse: bool = False) -> Graph:
+    return Graph(graph, stream, with_reverse)
+
+
+def validate(g: Graph, gfd, **opts) -> Result:
+    return g.validate(gfd, **opts)
+
+
+def validate_batch(g: Graph, gfds, **opts) -> list:
+    return g.validate_batch(gfds, **opts)

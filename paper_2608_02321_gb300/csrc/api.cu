@@ -1,0 +1,102 @@
+// C-ABI entry points declared in include/gfd.h.
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "engine.h"
+
+namespace gfd {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+const char* last_error_cstr() { return g_last_error.c_str(); }
+
+void set_error(int code, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = std::string("[code ") + std::to_string(code) + "] " + buf;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    cudaGetLastError();
+    set_error(GFD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return GFD_ERR_CUDA;
+}
+
+}  // namespace gfd
+
+extern "C" {
+
+int gfd_graph_load(const gfd_graph_desc* desc, const gfd_opts* opts, gfd_graph** out) {
+    return gfd::graph_load(desc, opts, out);
+}
+
+void gfd_graph_free(gfd_graph* g) { gfd::graph_free(g); }
+
+int32_t gfd_graph_vertices(const gfd_graph* g) { return g ? g->n : 0; }
+int64_t gfd_graph_edges(const gfd_graph* g) { return g ? g->m : 0; }
+int64_t gfd_graph_device_bytes(const gfd_graph* g) { return g ? g->bytes : 0; }
+
+int gfd_validate(const gfd_graph* g, const gfd_gfd* phi, const gfd_opts* opts, gfd_result** out) {
+    if (!g || !phi || !out) {
+        gfd::set_error(GFD_ERR_INVALID_ARG, "gfd_validate: NULL argument");
+        return GFD_ERR_INVALID_ARG;
+    }
+    gfd_graph* gm = const_cast<gfd_graph*>(g);
+    std::lock_guard<std::mutex> lock(gm->mu);
+    const gfd_gfd* one[1] = {phi};
+    return gfd::run_batch(gm, one, 1, opts, out);
+}
+
+int gfd_validate_batch(const gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opts* opts,
+                       gfd_result** out) {
+    if (!g || !out || n < 0 || (n > 0 && !phis)) {
+        gfd::set_error(GFD_ERR_INVALID_ARG, "gfd_validate_batch: NULL argument");
+        return GFD_ERR_INVALID_ARG;
+    }
+    gfd_graph* gm = const_cast<gfd_graph*>(g);
+    std::lock_guard<std::mutex> lock(gm->mu);
+    return gfd::run_batch(gm, phis, n, opts, out);
+}
+
+uint64_t gfd_result_matches(const gfd_result* r) { return r ? r->n_matches : 0; }
+uint64_t gfd_result_violations(const gfd_result* r) { return r ? r->n_viol : 0; }
+int32_t gfd_result_arity(const gfd_result* r) { return r ? r->k : 0; }
+
+const int32_t* gfd_result_tuples(gfd_result* r) {
+    if (!r) {
+        gfd::set_error(GFD_ERR_INVALID_ARG, "gfd_result_tuples: NULL result");
+        return nullptr;
+    }
+    if (gfd::result_fetch(r) != GFD_OK) return nullptr;
+    return r->tuples.empty() ? nullptr : r->tuples.data();
+}
+
+double gfd_result_profile(const gfd_result* r, int32_t which, int64_t* launches) {
+    if (!r || which < 0 || which >= 5) {
+        if (launches) *launches = 0;
+        return 0.0;
+    }
+    if (launches) *launches = r->prof_launch[which];
+    return r->prof_ms[which];
+}
+
+uint64_t gfd_result_stat(const gfd_result* r, int32_t which) {
+    if (!r || which < 0 || which >= 6) return 0;
+    return r->stat[which];
+}
+
+void gfd_result_free(gfd_result* r) {
+    if (!r) return;
+    if (r->d_viol) cudaFree(r->d_viol);
+    delete r;
+}
+
+const char* gfd_last_error(void) { return gfd::last_error_cstr(); }
+
+}  // extern "C"

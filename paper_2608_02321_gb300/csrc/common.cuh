@@ -1,0 +1,173 @@
+// Internal structures shared by the library's translation units.
+//
+// Device data layout (all resident in HBM):
+//   graph:   out_off/in_off u32 [V+1]; out_adj/in_adj u32 [E] packed as
+//            (neighbour << lbits) | edge_label, rows sorted by neighbour;
+//            vinfo u32 [V] = vertex label (low 16 bits) | (self-loop label + 1) << 16
+//            (0 in the high half = no self-loop); attrs i32 [n_attrs][V].
+//   index:   per (GFD, level) a candidate bitmap [nwords] u32, its exclusive
+//            popcount prefix [nwords] u32 (so rank(v) is O(1)), the sorted
+//            candidate list i32, and for every level i >= 1 the index edges of
+//            the spanning-tree edge (parent(i), i): off u32 [|C(parent)|+1],
+//            idx i32 [nnz] = positions in C(i).
+//   frontier: per (GFD, level l >= 1) a buffer of partial matches, row-major
+//            [chunk][2(l+1)] i32 = l+1 vertex ids then l+1 candidate positions,
+//            plus the exclusive prefix of each row's fan-out u64 [chunk].
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gfd.h"
+
+namespace gfd {
+
+constexpr int MAXK = 16;
+constexpr int MAXLIT = 32;
+// expectation for an ordered vertex pair of the pattern
+constexpr int16_t EXP_SKIP = -3;  // already guaranteed by construction
+constexpr int16_t EXP_NONE = -2;  // the data graph must have no such edge
+constexpr int16_t EXP_ANY = -1;   // an edge with any label
+constexpr int32_t NOEDGE = -2;
+
+// packed per-level counter: rows in the high ROW_BITS bits, fan-out sum below
+constexpr int ROW_SHIFT = 40;
+constexpr uint64_t WORK_MASK = (1ull << ROW_SHIFT) - 1;
+
+struct DevGraph {
+    int32_t n;
+    int32_t n_attrs;
+    int32_t lbits;
+    uint32_t lmask;
+    int64_t m;
+    uint32_t nwords;  // ceil(V / 32)
+    const uint32_t* out_off;
+    const uint32_t* in_off;
+    const uint32_t* out_adj;
+    const uint32_t* in_adj;
+    const uint32_t* vinfo;
+    const int32_t* attrs;
+};
+
+// Candidate filter key (Section III.B step 1a-1b): label, degree lower bounds
+// (self-loops excluded on both sides) and the self-loop expectation.
+struct FilterKey {
+    int32_t label;     // or GFD_WILDCARD
+    uint32_t dout_min;
+    uint32_t din_min;
+    int32_t self_exp;  // EXP_NONE, EXP_ANY or a label
+};
+
+struct LevelPlan {
+    int8_t u;          // pattern node matched at this level
+    int8_t par;        // level of its spanning-tree parent (-1 at level 0)
+    int8_t tdir;       // 1: tree edge parent -> u, 0: u -> parent
+    int8_t nchk;       // number of entries in chk_q
+    int32_t tlab;      // tree edge label or GFD_WILDCARD
+    uint32_t inj;      // bit q: v must differ from the vertex at level q
+    int8_t chk_q[2 * MAXK];   // earlier level of each pair check
+    int8_t chk_dir[2 * MAXK]; // 1: edge u -> node(q), 0: node(q) -> u
+    int16_t chk_exp[2 * MAXK];// expectation (EXP_NONE / EXP_ANY / label)
+};
+
+struct DevLit {
+    int32_t kind;  // 0: x.A = c, 1: x.A = y.B
+    int32_t xl;    // level of x
+    int32_t a;
+    int32_t yl;    // level of y
+    int32_t b;
+    int32_t c;
+};
+
+// Everything the device needs about one GFD slot.
+struct SlotDesc {
+    int32_t k;
+    int32_t nx, ny, y_false;
+    int32_t order[MAXK];
+    LevelPlan lv[MAXK];
+    DevLit lit[MAXLIT];  // X literals then Y literals
+    // index
+    uint32_t* bm[MAXK];
+    uint32_t* rank[MAXK];
+    int32_t* cand[MAXK];
+    uint32_t cand_cap[MAXK];
+    uint32_t* cpi_off[MAXK];  // level i >= 1
+    int32_t* cpi_idx[MAXK];
+    uint64_t cpi_cap[MAXK];
+    // frontier
+    int32_t* rows[MAXK];      // level l >= 1
+    uint64_t* wpre[MAXK];     // level l >= 1
+    uint64_t chunk;           // max work items per step (= row capacity)
+    // output
+    int32_t* viol;
+    uint64_t viol_cap;
+};
+
+// Mutable per-slot state (device).
+struct SlotState {
+    int32_t cur;        // level being expanded, -1 when finished
+    int32_t err;
+    uint32_t ncand[MAXK];     // candidate list sizes
+    uint64_t nrows[MAXK];     // rows held at level l
+    uint64_t total[MAXK];     // work items at level l
+    uint64_t cursor[MAXK];    // work items of level l already expanded
+    uint64_t ctr[MAXK];       // packed rows/work counter of level l (filled by l-1)
+    uint64_t cb, ce;          // current step's work range at level `cur`
+    uint64_t n_matches;
+    uint64_t n_viol;
+    uint64_t st_work, st_rows, st_probes, st_steps, st_cpi;
+};
+
+// Scheduler state shared by all slots of a run (device).
+struct Sched {
+    int32_t n_slots;
+    int32_t active;
+    int32_t err;
+    uint32_t total_tiles;
+    uint32_t tile;            // work items per tile
+    uint32_t bar_count;       // grid barrier
+    uint32_t bar_gen;
+    uint32_t pad;
+    uint64_t steps;
+    uint64_t timeout_ns;      // limit of one grid-barrier wait
+    uint64_t probes;
+    uint64_t t_start;         // globaltimer at the first step
+    uint64_t run_limit_ns;    // limit of the whole enumeration
+};
+
+// device error codes (Sched::err, SlotState::err)
+enum : int32_t {
+    DERR_NONE = 0,
+    DERR_COUNTER_OVERFLOW = 1,
+    DERR_TIMEOUT = 2,
+    DERR_CAPACITY = 3,
+};
+
+__host__ __device__ inline bool label_ok(int32_t want, int32_t have) {
+    return want == GFD_WILDCARD || want == have;
+}
+
+// Agreement of a pattern expectation with a data-graph edge label (NOEDGE if
+// the edge is absent): Section II, (a,b) ∈ E_Q ⇔ (h(a),h(b)) ∈ E with equal labels.
+__host__ __device__ inline bool exp_ok(int32_t e, int32_t gl) {
+    if (e == EXP_NONE) return gl == NOEDGE;
+    if (gl == NOEDGE) return false;
+    return e == EXP_ANY || e == gl;
+}
+
+// ---------------------------------------------------------------- host side
+struct Status {
+    int code = GFD_OK;
+    const char* where = "";
+};
+
+void set_error(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define GFD_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t _e = (call);                                \
+        if (_e != cudaSuccess) return ::gfd::cuda_fail(_e, #call); \
+    } while (0)
+
+}  // namespace gfd

@@ -1,0 +1,118 @@
+// Host-side handles and the engine interface shared by the translation units.
+#pragma once
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "plan.h"
+
+namespace gfd {
+struct Engine;
+}
+
+struct gfd_graph {
+    int32_t n = 0;
+    int64_t m = 0;
+    int32_t n_attrs = 0;
+    int32_t lbits = 1;
+    int64_t bytes = 0;
+    gfd::DevGraph dg{};
+    std::vector<void*> allocs;
+    std::vector<unsigned long long> label_stats;  // [65536][count, out-degree sum, in-degree sum]
+    cudaStream_t stream = nullptr;
+    gfd::Engine* eng = nullptr;
+    std::mutex mu;
+};
+
+struct gfd_result {
+    int32_t k = 0;
+    uint64_t n_matches = 0;
+    uint64_t n_viol = 0;
+    int32_t* d_viol = nullptr;  // device, unsorted, owned by the result
+    bool fetched = false;
+    std::vector<int32_t> tuples;
+    double prof_ms[5] = {0, 0, 0, 0, 0};
+    int64_t prof_launch[5] = {0, 0, 0, 0, 0};
+    uint64_t stat[6] = {0, 0, 0, 0, 0, 0};
+    cudaStream_t stream = nullptr;
+};
+
+namespace gfd {
+
+// ---- job descriptors of the index kernels (device memory)
+struct AndJob {          // bm = src & tmp[0] & ... & tmp[ntmp-1]
+    uint32_t* bm;
+    const uint32_t* src;
+    const uint32_t* tmp[2 * MAXK];
+    int32_t ntmp;
+};
+struct CompactJob {      // rank and candidate list of bm
+    const uint32_t* bm;
+    uint32_t* rank;
+    int32_t* cand;
+    uint32_t* count;
+};
+struct ScatterJob {      // mark vertices adjacent to the candidates of another level
+    const int32_t* qcand;
+    const uint32_t* qcount;
+    const uint32_t* filter;  // only vertices in this bitmap are marked
+    uint32_t* marks;
+    int32_t scan_out;        // 1: follow out-edges of qcand, 0: in-edges
+    int32_t lab;
+};
+struct PruneJob {        // drop candidates with no neighbour in a later level
+    const int32_t* cand;
+    const uint32_t* count;
+    uint32_t* bm;
+    int32_t ncon;
+    const uint32_t* con_bm[2 * MAXK];
+    int32_t con_dir[2 * MAXK];
+    int32_t con_lab[2 * MAXK];
+};
+struct CpiJob {          // index edges of one spanning-tree edge
+    const int32_t* pcand;
+    const uint32_t* pcount;
+    const uint32_t* cbm;
+    const uint32_t* crank;
+    uint32_t* off;
+    int32_t* idx;
+    uint64_t cap;
+    int32_t out;             // 1: children are out-neighbours of the parent candidates
+    int32_t lab;
+    uint64_t* nnz_stat;
+};
+
+// ---- index kernels (index.cu); each launch covers all jobs given
+int launch_filter(const DevGraph& g, const FilterKey* d_keys, int nkeys, uint32_t* d_out, cudaStream_t st);
+int launch_and(const DevGraph& g, const AndJob* d_jobs, int njobs, cudaStream_t st);
+int launch_compact(const DevGraph& g, const CompactJob* d_jobs, int njobs, cudaStream_t st);
+int launch_scatter(const DevGraph& g, const ScatterJob* d_jobs, int njobs, cudaStream_t st);
+int launch_prune(const DevGraph& g, const PruneJob* d_jobs, int njobs, cudaStream_t st);
+int launch_cpi(const DevGraph& g, const CpiJob* d_jobs, int njobs, int32_t* d_err, cudaStream_t st);
+
+// ---- enumeration (enumerate.cu)
+struct EnumArgs {
+    DevGraph g;
+    const SlotDesc* slots;
+    SlotState* state;
+    Sched* sched;
+    uint32_t* tile_base;  // [n_slots + 1]
+    int32_t n_slots;
+    int32_t tile;         // work items per tile
+};
+int enum_init(const EnumArgs& a, cudaStream_t st);
+// Runs supersteps until every slot is finished. persistent: one cooperative
+// launch; else a host loop (optionally captured into CUDA graphs).
+int enum_run(const EnumArgs& a, bool persistent, bool use_graph, int block_threads, cudaStream_t st,
+             cudaEvent_t ev0, cudaEvent_t ev1, int64_t* launches);
+
+// ---- orchestration (run.cu)
+int graph_load(const gfd_graph_desc* d, const gfd_opts* o, gfd_graph** out);
+void graph_free(gfd_graph* g);
+void engine_free(Engine* e);
+int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opts* o, gfd_result** out);
+int result_fetch(gfd_result* r);
+
+}  // namespace gfd

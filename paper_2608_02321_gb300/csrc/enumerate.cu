@@ -1,0 +1,516 @@
+// Core-first match enumeration over the compact path index (Section III.B,
+// step 2) with the literal check and violation output (Section II) fused into
+// the last level.
+//
+// Execution model: a breadth-first / depth-first hybrid over many GFD slots at
+// once. Each slot keeps one buffer of partial matches per level. A step takes
+// a bounded chunk of "work items" from the deepest unfinished level of every
+// active slot: work item w of level l is the pair (partial match r, o-th index
+// edge of r's tree parent), found by binary search in the exclusive prefix of
+// the rows' fan-outs, so hub vertices are split evenly over threads. Each work
+// item yields at most one partial match of level l+1, so a level-l chunk of
+// `chunk` items always fits the next buffer; when a level is exhausted the slot
+// pops back to the previous level (depth-first), bounding memory.
+//
+// A candidate v for pattern node u = order[i] extending partial match m passes
+// when: v != m[q] for earlier label-compatible levels q (injectivity), and for
+// every earlier level q and both directions, the data-graph edge between v and
+// m[q] agrees with the pattern (present with an equal label where Q has the
+// edge, absent where it has not: a match may not contain additional edges,
+// Section II; the CFL-Match index alone would allow them, Section III). The
+// spanning-tree edge to the parent is guaranteed by the index and skipped.
+//
+// Survivors are appended with one atomic per block on a packed 64-bit counter
+// (rows << 40 | fan-out sum), which gives each row both its index and the
+// exclusive prefix of fan-outs needed by the next step's search, consistently.
+//
+// The scheduler (k_control) runs in one block between steps. Two drivers: a
+// persistent cooperative kernel with a bounded grid barrier between phases, or
+// a host loop of (expand, control) launches, optionally captured in CUDA graphs.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+
+#include "engine.h"
+
+namespace gfd {
+
+namespace {
+
+constexpr int CTRL_THREADS = 1024;
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Label of the data-graph edge a -> b, or NOEDGE: binary search in the shorter
+// of out(a) and in(b) (both sorted by neighbour id).
+__device__ __forceinline__ int32_t edge_label(const DevGraph& g, uint32_t a, uint32_t a_out0, uint32_t a_out1,
+                                              uint32_t b, uint32_t b_in0, uint32_t b_in1) {
+    const uint32_t* arr;
+    uint32_t lo, hi, key;
+    if (a_out1 - a_out0 <= b_in1 - b_in0) {
+        arr = g.out_adj;
+        lo = a_out0;
+        hi = a_out1;
+        key = b;
+    } else {
+        arr = g.in_adj;
+        lo = b_in0;
+        hi = b_in1;
+        key = a;
+    }
+    const uint32_t end = hi;
+    const uint32_t kk = key << g.lbits;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(arr + mid) < kk) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo < end) {
+        const uint32_t p = __ldg(arr + lo);
+        if ((p >> g.lbits) == key) return (int32_t)(p & g.lmask);
+    }
+    return NOEDGE;
+}
+
+__device__ __forceinline__ bool lit_holds(const DevGraph& g, const DevLit& L, const uint32_t* m) {
+    const int32_t va = __ldg(g.attrs + (uint64_t)L.a * g.n + m[L.xl]);
+    if (va == GFD_ATTR_ABSENT) return false;
+    if (L.kind == 0) return va == L.c;
+    const int32_t vb = __ldg(g.attrs + (uint64_t)L.b * g.n + m[L.yl]);
+    return vb != GFD_ATTR_ABSENT && va == vb;
+}
+
+// Largest r in [0, n) with S[r] <= w (S non-decreasing, S[0] <= w). The index
+// offsets are read-only during enumeration; the frontier prefix is rewritten
+// between steps, so it is read through L2 only (ld.global.cg).
+__device__ __forceinline__ uint32_t find_row(const uint32_t* S, uint64_t n, uint64_t w) {
+    uint64_t lo = 0, hi = n;  // invariant: S[lo] <= w, answer in [lo, hi)
+    while (hi - lo > 1) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if ((uint64_t)__ldg(S + mid) <= w) lo = mid;
+        else hi = mid;
+    }
+    return (uint32_t)lo;
+}
+__device__ __forceinline__ uint32_t find_row(const uint64_t* S, uint64_t n, uint64_t w) {
+    uint64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (__ldcg((const unsigned long long*)S + mid) <= w) lo = mid;
+        else hi = mid;
+    }
+    return (uint32_t)lo;
+}
+
+template <int NT>
+__device__ void expand_tiles(const EnumArgs& A) {
+    using Scan = cub::BlockScan<uint64_t, NT>;
+    using Reduce = cub::BlockReduce<uint64_t, NT>;
+    __shared__ union {
+        typename Scan::TempStorage scan;
+        typename Reduce::TempStorage reduce;
+    } tmp;
+    __shared__ uint64_t sh_base;
+    __shared__ int32_t sh_slot;
+    const DevGraph& g = A.g;
+    const uint32_t total_tiles = *(volatile uint32_t*)&A.sched->total_tiles;
+    uint64_t probes = 0;
+    for (uint32_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        if (threadIdx.x == 0) {
+            // slot of tile t: largest s with tile_base[s] <= t
+            int lo = 0, hi = A.n_slots;
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (__ldcg(A.tile_base + mid) <= t) lo = mid;
+                else hi = mid;
+            }
+            sh_slot = lo;
+        }
+        __syncthreads();
+        const int s = sh_slot;
+        const SlotDesc* __restrict__ D = A.slots + s;
+        SlotState* S = A.state + s;
+        const int k = D->k;
+        // scheduler fields are rewritten between steps: read them through L2
+        const int l = __ldcg(&S->cur);
+        const int i = k == 1 ? 0 : l + 1;  // level being matched
+        const bool last = i == k - 1;
+        const uint64_t wb = __ldcg((const unsigned long long*)&S->cb) +
+                            (uint64_t)(t - __ldcg(A.tile_base + s)) * A.tile;
+        const uint64_t we = min(wb + (uint64_t)A.tile, (uint64_t)__ldcg((const unsigned long long*)&S->ce));
+        const LevelPlan& LP = D->lv[i];
+        // row source
+        const uint32_t* S0 = i > 0 ? D->cpi_off[i] : nullptr;
+        const uint64_t* Sl = l >= 1 ? D->wpre[l] : nullptr;
+        const int32_t* rows_l = l >= 1 ? D->rows[l] : nullptr;
+        const uint64_t nrows = k == 1 ? 0 : (l == 0 ? (uint64_t)S->ncand[0]
+                                                    : (uint64_t)__ldcg((const unsigned long long*)&S->nrows[l]));
+        const int rw = 2 * (l + 1);  // row width at level l
+        for (uint64_t w0 = wb; w0 < we; w0 += NT) {
+            const uint64_t w = w0 + threadIdx.x;
+            bool ok = w < we;
+            uint32_t m[MAXK];
+            uint32_t v = 0;
+            int32_t j = 0;
+            const int32_t* rowp = nullptr;
+            uint32_t r = 0;
+            if (ok) {
+                if (k == 1) {
+                    j = (int32_t)w;
+                    v = (uint32_t)D->cand[0][j];
+                } else {
+                    uint64_t o;
+                    uint32_t pp;
+                    if (l == 0) {
+                        r = find_row(S0, nrows, w);
+                        o = w - S0[r];
+                        pp = r;
+                        m[0] = (uint32_t)D->cand[0][r];
+                    } else {
+                        r = find_row(Sl, nrows, w);
+                        o = w - __ldcg((const unsigned long long*)Sl + r);
+                        rowp = rows_l + (uint64_t)r * rw;
+                        for (int q = 0; q <= l; q++) m[q] = (uint32_t)__ldcg(rowp + q);
+                        pp = (uint32_t)__ldcg(rowp + l + 1 + LP.par);
+                    }
+                    const uint32_t base = D->cpi_off[i][pp];
+                    j = D->cpi_idx[i][base + o];
+                    v = (uint32_t)D->cand[i][j];
+                    // injectivity
+                    for (int q = 0; q <= l; q++)
+                        if (((LP.inj >> q) & 1u) && m[q] == v) ok = false;
+                    // every other pattern pair, both directions
+                    if (ok && LP.nchk > 0) {
+                        const uint32_t vo0 = g.out_off[v], vo1 = g.out_off[v + 1];
+                        const uint32_t vi0 = g.in_off[v], vi1 = g.in_off[v + 1];
+                        for (int c = 0; c < LP.nchk && ok; c++) {
+                            const uint32_t x = m[LP.chk_q[c]];
+                            int32_t gl;
+                            if (LP.chk_dir[c]) gl = edge_label(g, v, vo0, vo1, x, g.in_off[x], g.in_off[x + 1]);
+                            else gl = edge_label(g, x, g.out_off[x], g.out_off[x + 1], v, vi0, vi1);
+                            probes++;
+                            ok = exp_ok(LP.chk_exp[c], gl);
+                        }
+                    }
+                }
+                m[i] = v;
+            }
+            if (last) {
+                // complete match: count it, check X -> Y, emit a violation
+                bool viol = false;
+                if (ok) {
+                    bool x_ok = true;
+                    for (int q = 0; q < D->nx && x_ok; q++) x_ok = lit_holds(g, D->lit[q], m);
+                    if (x_ok) {
+                        bool y_ok = !D->y_false;
+                        for (int q = 0; q < D->ny && y_ok; q++) y_ok = lit_holds(g, D->lit[D->nx + q], m);
+                        viol = !y_ok;
+                    }
+                }
+                const uint64_t packed = ((uint64_t)ok << 32) | (uint64_t)viol;
+                uint64_t excl, total;
+                Scan(tmp.scan).ExclusiveSum(packed, excl, total);
+                if (threadIdx.x == 0) {
+                    if (total >> 32) atomicAdd((unsigned long long*)&S->n_matches, (unsigned long long)(total >> 32));
+                    sh_base = (total & 0xffffffffu)
+                                  ? atomicAdd((unsigned long long*)&S->n_viol, (unsigned long long)(total & 0xffffffffu))
+                                  : 0;
+                }
+                __syncthreads();
+                if (viol) {
+                    const uint64_t idx = sh_base + (excl & 0xffffffffu);
+                    if (idx < D->viol_cap) {
+                        int32_t* out = D->viol + idx * k;
+                        for (int q = 0; q < k; q++) out[D->order[q]] = (int32_t)m[q];
+                    }
+                }
+            } else {
+                // partial match of level i: append with its fan-out for level i+1
+                uint64_t fo = 0;
+                if (ok) {
+                    const int pn = D->lv[i + 1].par;
+                    const uint32_t ppn = pn == i ? (uint32_t)j : (l == 0 ? r : (uint32_t)__ldcg(rowp + l + 1 + pn));
+                    const uint32_t* co = D->cpi_off[i + 1];
+                    fo = co[ppn + 1] - co[ppn];
+                }
+                const uint64_t packed = ok ? ((1ull << ROW_SHIFT) | fo) : 0ull;
+                uint64_t excl, total;
+                Scan(tmp.scan).ExclusiveSum(packed, excl, total);
+                if (threadIdx.x == 0) {
+                    uint64_t old = 0;
+                    if (total) {
+                        old = atomicAdd((unsigned long long*)&S->ctr[i], (unsigned long long)total);
+                        if ((old & WORK_MASK) + (total & WORK_MASK) > WORK_MASK ||
+                            (old >> ROW_SHIFT) + (total >> ROW_SHIFT) > D->chunk)
+                            atomicExch(&S->err, DERR_COUNTER_OVERFLOW);
+                    }
+                    sh_base = old;
+                }
+                __syncthreads();
+                if (ok) {
+                    const uint64_t row = (sh_base >> ROW_SHIFT) + (excl >> ROW_SHIFT);
+                    if (row < D->chunk) {
+                        const int nw = 2 * (i + 1);
+                        int32_t* dst = D->rows[i] + row * nw;
+                        for (int q = 0; q <= i; q++) dst[q] = (int32_t)m[q];
+                        if (l == 0) {
+                            dst[i + 1] = (int32_t)r;
+                        } else {
+                            for (int q = 0; q <= l; q++) dst[i + 1 + q] = __ldcg(rowp + l + 1 + q);
+                        }
+                        dst[i + 1 + i] = j;
+                        D->wpre[i][row] = (sh_base & WORK_MASK) + (excl & WORK_MASK);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+    }
+    // probe statistics: one atomic per block
+    const uint64_t p = Reduce(tmp.reduce).Sum(probes);
+    if (threadIdx.x == 0 && p) atomicAdd((unsigned long long*)&A.sched->probes, (unsigned long long)p);
+}
+
+// One block: finish the last step of every slot and plan the next one.
+template <int CT>
+__device__ void control_step(const EnumArgs& A, bool first) {
+    using Scan = cub::BlockScan<uint32_t, CT>;
+    __shared__ typename Scan::TempStorage tmp;
+    __shared__ uint32_t carry_s;
+    __shared__ int32_t active_s;
+    __shared__ int32_t expired_s;
+    if (threadIdx.x == 0) {
+        carry_s = 0;
+        active_s = 0;
+        // bound the whole enumeration in time: past the limit every slot stops
+        const uint64_t now = globaltimer_ns();
+        if (first || A.sched->t_start == 0) A.sched->t_start = now;
+        expired_s = now - A.sched->t_start > A.sched->run_limit_ns;
+        if (expired_s) A.sched->err = DERR_TIMEOUT;
+    }
+    __syncthreads();
+    for (int base = 0; base < A.n_slots; base += CT) {
+        const int s = base + threadIdx.x;
+        uint32_t tiles = 0;
+        if (s < A.n_slots) {
+            const SlotDesc* D = A.slots + s;
+            SlotState* S = A.state + s;
+            const int k = D->k;
+            if (first) {
+                S->cur = 0;
+                S->cursor[0] = 0;
+                S->nrows[0] = S->ncand[0];
+                S->total[0] = k == 1 ? (uint64_t)S->ncand[0] : (uint64_t)D->cpi_off[1][S->ncand[0]];
+            } else if (S->cur >= 0) {
+                const int l = S->cur;
+                S->cursor[l] = S->ce;
+                S->st_steps++;
+                if (k > 1 && l + 1 <= k - 2) {
+                    const uint64_t c = __ldcg((const unsigned long long*)&S->ctr[l + 1]);
+                    const uint64_t rows = c >> ROW_SHIFT;
+                    if (rows > 0) {
+                        S->nrows[l + 1] = rows;
+                        S->total[l + 1] = c & WORK_MASK;
+                        S->cursor[l + 1] = 0;
+                        S->cur = l + 1;
+                        S->st_rows += rows;
+                    }
+                }
+            }
+            while (S->cur >= 0 && S->cursor[S->cur] >= S->total[S->cur]) S->cur--;
+            if (__ldcg(&S->err) || expired_s) S->cur = -1;
+            if (S->cur >= 0) {
+                const int l = S->cur;
+                S->cb = S->cursor[l];
+                S->ce = min(S->cb + D->chunk, S->total[l]);
+                if (k > 1 && l + 1 <= k - 2) S->ctr[l + 1] = 0;
+                tiles = (uint32_t)((S->ce - S->cb + A.tile - 1) / A.tile);
+                S->st_work += S->ce - S->cb;
+                atomicAdd(&active_s, 1);
+            }
+        }
+        uint32_t excl, total;
+        Scan(tmp).ExclusiveSum(tiles, excl, total);
+        if (s < A.n_slots) A.tile_base[s] = carry_s + excl;
+        __syncthreads();
+        if (threadIdx.x == 0) carry_s += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        A.tile_base[A.n_slots] = carry_s;
+        A.sched->total_tiles = carry_s;
+        A.sched->active = active_s;
+        A.sched->steps++;
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(CTRL_THREADS) k_control(EnumArgs A, int first) {
+    control_step<CTRL_THREADS>(A, first != 0);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_expand(EnumArgs A) {
+    expand_tiles<NT>(A);
+}
+
+// Bounded grid barrier (cooperative launch guarantees co-residency): the last
+// arriving block bumps the generation; the others wait for it, up to
+// sched->timeout_ns, after which they record DERR_TIMEOUT and give up.
+__device__ bool grid_barrier(Sched* s) {
+    __syncthreads();
+    __shared__ int ok_s;
+    if (threadIdx.x == 0) {
+        volatile uint32_t* genp = &s->bar_gen;
+        const uint32_t gen = *genp;
+        __threadfence();
+        const uint32_t arrived = atomicAdd(&s->bar_count, 1u);
+        int ok = 1;
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&s->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&s->bar_gen, 1u);
+        } else {
+            const uint64_t t0 = globaltimer_ns();
+            while (*genp == gen) {
+                if (*(volatile int32_t*)&s->err) {
+                    ok = 0;
+                    break;
+                }
+                if (globaltimer_ns() - t0 > s->timeout_ns) {
+                    atomicExch(&s->err, DERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_persistent(EnumArgs A) {
+    for (;;) {
+        expand_tiles<NT>(A);
+        if (!grid_barrier(A.sched)) return;
+        if (blockIdx.x == 0) control_step<NT>(A, false);
+        if (!grid_barrier(A.sched)) return;
+        if (*(volatile int32_t*)&A.sched->active == 0) return;
+    }
+}
+
+template <int NT>
+int launch_persistent(const EnumArgs& a, cudaStream_t st, int64_t* launches) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<NT>, NT, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm < 1) {
+        set_error(GFD_ERR_CUDA, "persistent enumeration kernel cannot be resident");
+        return GFD_ERR_CUDA;
+    }
+    const int grid = sms * per_sm;
+    EnumArgs args = a;
+    void* params[] = {&args};
+    e = cudaLaunchCooperativeKernel((const void*)k_persistent<NT>, dim3(grid), dim3(NT), params, 0, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel");
+    if (launches) *launches += 1;
+    return GFD_OK;
+}
+
+template <int NT>
+int expand_grid() {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand<NT>, NT, 0);
+    return sms * std::max(per_sm, 1);
+}
+
+template <int NT>
+int host_loop(const EnumArgs& a, bool use_graph, cudaStream_t st, int64_t* launches) {
+    const int grid = expand_grid<NT>();
+    int32_t* h_active = nullptr;
+    cudaError_t e = cudaMallocHost(&h_active, sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+    const int per_check = 8;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    int rc = GFD_OK;
+    if (use_graph) {
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int it = 0; it < per_check; it++) {
+                k_expand<NT><<<grid, NT, 0, st>>>(a);
+                k_control<<<1, CTRL_THREADS, 0, st>>>(a, 0);
+            }
+            e = cudaStreamEndCapture(st, &graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) {
+            cudaFreeHost(h_active);
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(e, "CUDA graph capture of the enumeration steps");
+        }
+    }
+    for (int64_t round = 0;; round++) {
+        if (use_graph) {
+            e = cudaGraphLaunch(exec, st);
+            if (launches) *launches += 2 * per_check;
+        } else {
+            for (int it = 0; it < per_check; it++) {
+                k_expand<NT><<<grid, NT, 0, st>>>(a);
+                k_control<<<1, CTRL_THREADS, 0, st>>>(a, 0);
+            }
+            e = cudaGetLastError();
+            if (launches) *launches += 2 * per_check;
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_active, &a.sched->active, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "enumeration step");
+            break;
+        }
+        if (*h_active == 0) break;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaFreeHost(h_active);
+    return rc;
+}
+
+}  // namespace
+
+int enum_init(const EnumArgs& a, cudaStream_t st) {
+    k_control<<<1, CTRL_THREADS, 0, st>>>(a, 1);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GFD_OK : cuda_fail(e, "k_control");
+}
+
+int enum_run(const EnumArgs& a, bool persistent, bool use_graph, int block_threads, cudaStream_t st,
+             cudaEvent_t ev0, cudaEvent_t ev1, int64_t* launches) {
+    if (ev0) cudaEventRecord(ev0, st);
+    int rc;
+    if (persistent) {
+        rc = block_threads == 512 ? launch_persistent<512>(a, st, launches)
+                                  : launch_persistent<256>(a, st, launches);
+    } else {
+        rc = block_threads == 512 ? host_loop<512>(a, use_graph, st, launches)
+                                  : host_loop<256>(a, use_graph, st, launches);
+    }
+    if (ev1) cudaEventRecord(ev1, st);
+    return rc;
+}
+
+}  // namespace gfd

@@ -1,0 +1,267 @@
+// Host-side planning of one GFD; see plan.h.
+//
+// Core-first decomposition (Section III.B, step 2a; the idea of postponing
+// Cartesian products, Section III): the core is the 2-core of the undirected
+// skeleton of Q (the vertices left after repeatedly removing vertices of
+// degree <= 1). Non-core vertices of skeleton degree > 1 form the forest, the
+// rest are leaves. The matching order is the core in breadth-first order from
+// the root, then the forest, then the leaves. The root (the vertex v_q from
+// which the compact path index is built, Section III.B step 1a) is the core
+// vertex with the fewest label candidates per skeleton edge. The spanning
+// tree of the index (step 1d) links every later vertex to its earliest-ordered
+// skeleton neighbour; all other pattern pairs are checked after a tree match is
+// found, including pairs WITHOUT a pattern edge, since a match may not contain
+// additional edges (Section II, match definition; Section III on CFL-Match).
+#include "plan.h"
+
+#include <algorithm>
+#include <cstring>
+
+namespace gfd {
+
+namespace {
+
+int32_t exp_of(int32_t qlab) { return qlab == NOEDGE ? EXP_NONE : qlab; }
+
+}  // namespace
+
+int make_plan(const gfd_gfd* phi, int32_t n_attrs, const unsigned long long* label_stats,
+              int64_t n_vertices, HostPlan* P) {
+    if (!phi) {
+        set_error(GFD_ERR_INVALID_ARG, "NULL GFD");
+        return GFD_ERR_INVALID_ARG;
+    }
+    const int k = phi->k;
+    if (k < 1 || !phi->node_label) {
+        set_error(GFD_ERR_INVALID_ARG, "pattern needs k >= 1 nodes and node labels");
+        return GFD_ERR_INVALID_ARG;
+    }
+    if (k > MAXK) {
+        set_error(GFD_ERR_UNSUPPORTED, "pattern has %d nodes, limit is %d", k, MAXK);
+        return GFD_ERR_UNSUPPORTED;
+    }
+    if (phi->m < 0 || (phi->m > 0 && (!phi->esrc || !phi->edst || !phi->elabel))) {
+        set_error(GFD_ERR_INVALID_ARG, "pattern edge arrays missing");
+        return GFD_ERR_INVALID_ARG;
+    }
+    int32_t q[MAXK][MAXK];
+    for (int a = 0; a < MAXK; a++)
+        for (int b = 0; b < MAXK; b++) q[a][b] = NOEDGE;
+    for (int i = 0; i < k; i++) {
+        int32_t L = phi->node_label[i];
+        if (L < GFD_WILDCARD || L > 65534) {
+            set_error(GFD_ERR_INVALID_ARG, "node %d label %d out of range", i, L);
+            return GFD_ERR_INVALID_ARG;
+        }
+    }
+    for (int e = 0; e < phi->m; e++) {
+        int a = phi->esrc[e], b = phi->edst[e], l = phi->elabel[e];
+        if (a < 0 || a >= k || b < 0 || b >= k || l < GFD_WILDCARD || l > 255) {
+            set_error(GFD_ERR_INVALID_ARG, "pattern edge %d (%d -> %d, label %d) out of range", e, a, b, l);
+            return GFD_ERR_INVALID_ARG;
+        }
+        if (q[a][b] != NOEDGE) {
+            set_error(GFD_ERR_INVALID_ARG, "pattern edge %d -> %d given twice", a, b);
+            return GFD_ERR_INVALID_ARG;
+        }
+        q[a][b] = l;
+    }
+    const int nlit = phi->nx + (phi->y_false ? 0 : phi->ny);
+    if (phi->nx < 0 || phi->ny < 0 || (phi->nx > 0 && !phi->X) || (!phi->y_false && phi->ny > 0 && !phi->Y)) {
+        set_error(GFD_ERR_INVALID_ARG, "literal arrays missing");
+        return GFD_ERR_INVALID_ARG;
+    }
+    if (nlit > MAXLIT) {
+        set_error(GFD_ERR_UNSUPPORTED, "%d literals, limit is %d", nlit, MAXLIT);
+        return GFD_ERR_UNSUPPORTED;
+    }
+    // undirected skeleton (self-loops excluded)
+    bool adj[MAXK][MAXK];
+    int deg[MAXK];
+    for (int a = 0; a < k; a++) {
+        deg[a] = 0;
+        for (int b = 0; b < k; b++) {
+            adj[a][b] = a != b && (q[a][b] != NOEDGE || q[b][a] != NOEDGE);
+            deg[a] += adj[a][b];
+        }
+    }
+    {  // connected?
+        bool seen[MAXK] = {false};
+        int stack[MAXK], sp = 0, cnt = 1;
+        seen[0] = true;
+        stack[sp++] = 0;
+        while (sp) {
+            int a = stack[--sp];
+            for (int b = 0; b < k; b++)
+                if (adj[a][b] && !seen[b]) {
+                    seen[b] = true;
+                    cnt++;
+                    stack[sp++] = b;
+                }
+        }
+        if (cnt != k) {
+            set_error(GFD_ERR_UNSUPPORTED, "pattern is disconnected");
+            return GFD_ERR_UNSUPPORTED;
+        }
+    }
+    // 2-core by repeated removal of vertices of degree <= 1
+    bool core[MAXK];
+    {
+        int d[MAXK];
+        for (int a = 0; a < k; a++) {
+            core[a] = true;
+            d[a] = deg[a];
+        }
+        bool changed = true;
+        while (changed) {
+            changed = false;
+            for (int a = 0; a < k; a++)
+                if (core[a] && d[a] <= 1) {
+                    core[a] = false;
+                    changed = true;
+                    for (int b = 0; b < k; b++)
+                        if (adj[a][b] && core[b]) d[b]--;
+                }
+        }
+    }
+    bool any_core = false;
+    for (int a = 0; a < k; a++) any_core |= core[a];
+    // root: fewest label candidates per skeleton edge among core vertices
+    auto label_count = [&](int32_t L) -> double {
+        if (L == GFD_WILDCARD) return (double)n_vertices;
+        return (double)label_stats[3 * (size_t)L];
+    };
+    int root = 0;
+    double best = 1e300;
+    for (int a = 0; a < k; a++) {
+        if (any_core && !core[a]) continue;
+        double s = label_count(phi->node_label[a]) / (double)std::max(1, deg[a]);
+        if (s < best) {
+            best = s;
+            root = a;
+        }
+    }
+    // order: core BFS, then forest BFS, then leaves
+    int pos[MAXK];
+    for (int a = 0; a < k; a++) pos[a] = -1;
+    int nord = 0;
+    auto bfs = [&](auto allowed) {
+        for (int h = 0; h < nord; h++) {
+            int a = P->order[h];
+            for (int b = 0; b < k; b++)
+                if (adj[a][b] && pos[b] < 0 && allowed(b)) {
+                    pos[b] = nord;
+                    P->order[nord++] = b;
+                }
+        }
+    };
+    pos[root] = 0;
+    P->order[nord++] = root;
+    bfs([&](int b) { return core[b]; });
+    P->core_size = nord;
+    bfs([&](int b) { return !core[b] && deg[b] > 1; });
+    P->forest_end = nord;
+    bfs([&](int b) { return true; });
+    if (nord != k) {
+        set_error(GFD_ERR_INVALID_ARG, "internal: order incomplete");
+        return GFD_ERR_INVALID_ARG;
+    }
+    P->k = k;
+    for (int i = 0; i < k; i++) P->level_of[P->order[i]] = i;
+
+    for (int i = 0; i < k; i++) {
+        const int u = P->order[i];
+        LevelPlan& L = P->lv[i];
+        memset(&L, 0, sizeof(L));
+        L.u = (int8_t)u;
+        L.par = -1;
+        if (i > 0) {
+            for (int h = 0; h < i; h++)
+                if (adj[P->order[h]][u]) {
+                    L.par = (int8_t)h;
+                    break;
+                }
+            const int p = P->order[L.par];
+            if (q[p][u] != NOEDGE) {
+                L.tdir = 1;
+                L.tlab = q[p][u];
+            } else {
+                L.tdir = 0;
+                L.tlab = q[u][p];
+            }
+        }
+        // pair checks against every earlier level
+        int n = 0;
+        for (int h = 0; h < i; h++) {
+            const int w = P->order[h];
+            const int32_t lu = phi->node_label[u], lw = phi->node_label[w];
+            if (lu == GFD_WILDCARD || lw == GFD_WILDCARD || lu == lw) L.inj |= 1u << h;
+            const bool skip_out = h == L.par && L.tdir == 0;  // u -> parent is the tree edge
+            const bool skip_in = h == L.par && L.tdir == 1;   // parent -> u is the tree edge
+            if (!skip_out) {
+                L.chk_q[n] = (int8_t)h;
+                L.chk_dir[n] = 1;
+                L.chk_exp[n] = (int16_t)exp_of(q[u][w]);
+                n++;
+            }
+            if (!skip_in) {
+                L.chk_q[n] = (int8_t)h;
+                L.chk_dir[n] = 0;
+                L.chk_exp[n] = (int16_t)exp_of(q[w][u]);
+                n++;
+            }
+        }
+        L.nchk = (int8_t)n;
+        // candidate filter key (degrees without self-loops)
+        FilterKey& K = P->key[i];
+        K.label = phi->node_label[u];
+        K.dout_min = 0;
+        K.din_min = 0;
+        for (int w = 0; w < k; w++) {
+            if (w == u) continue;
+            K.dout_min += q[u][w] != NOEDGE;
+            K.din_min += q[w][u] != NOEDGE;
+        }
+        K.self_exp = exp_of(q[u][u]);
+        // refinement constraints
+        P->td[i].clear();
+        P->bu[i].clear();
+        for (int w = 0; w < k; w++) {
+            if (w == u) continue;
+            const int h = P->level_of[w];
+            if (q[u][w] != NOEDGE) (h < i ? P->td[i] : P->bu[i]).push_back(Con{(int8_t)h, 1, q[u][w]});
+            if (q[w][u] != NOEDGE) (h < i ? P->td[i] : P->bu[i]).push_back(Con{(int8_t)h, 0, q[w][u]});
+        }
+    }
+    // literals
+    P->lits.clear();
+    auto add_lit = [&](const gfd_literal& l) -> int {
+        if ((l.kind != 0 && l.kind != 1) || l.x < 0 || l.x >= k || l.a < 0 || l.a >= n_attrs ||
+            (l.kind == 1 && (l.y < 0 || l.y >= k || l.b < 0 || l.b >= n_attrs))) {
+            set_error(GFD_ERR_INVALID_ARG, "literal refers to a missing node or attribute");
+            return GFD_ERR_INVALID_ARG;
+        }
+        DevLit d;
+        d.kind = l.kind;
+        d.xl = P->level_of[l.x];
+        d.a = l.a;
+        d.yl = l.kind == 1 ? P->level_of[l.y] : 0;
+        d.b = l.kind == 1 ? l.b : 0;
+        d.c = l.c;
+        P->lits.push_back(d);
+        return GFD_OK;
+    };
+    for (int i = 0; i < phi->nx; i++)
+        if (int rc = add_lit(phi->X[i])) return rc;
+    P->nx = phi->nx;
+    P->y_false = phi->y_false ? 1 : 0;
+    P->ny = 0;
+    if (!P->y_false) {
+        for (int i = 0; i < phi->ny; i++)
+            if (int rc = add_lit(phi->Y[i])) return rc;
+        P->ny = phi->ny;
+    }
+    return GFD_OK;
+}
+
+}  // namespace gfd

@@ -1,0 +1,41 @@
+// Host-side planning of one GFD (Section III.B): core-first decomposition of
+// the pattern, root and spanning tree of the compact path index, matching
+// order, per-level checks of the remaining pattern pairs, filter keys,
+// refinement constraints and literal slots.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace gfd {
+
+// A refinement constraint on level `lvl`: every candidate x of that level needs
+// a neighbour in C(q), through an out-edge x -> y (dir 1) or an in-edge
+// y -> x (dir 0), with label `lab` (or any label for GFD_WILDCARD).
+struct Con {
+    int8_t q;
+    int8_t dir;
+    int32_t lab;
+};
+
+struct HostPlan {
+    int k = 0;
+    int order[MAXK];      // node at level
+    int level_of[MAXK];   // level of node
+    int core_size = 0;    // levels [0, core_size) are the core (2-core, or the root)
+    int forest_end = 0;   // levels [core_size, forest_end) are forest nodes, the rest leaves
+    LevelPlan lv[MAXK];
+    FilterKey key[MAXK];  // candidate filter key per level
+    std::vector<Con> td[MAXK];  // constraints from earlier levels
+    std::vector<Con> bu[MAXK];  // constraints from later levels
+    std::vector<DevLit> lits;   // X then Y
+    int nx = 0, ny = 0, y_false = 0;
+};
+
+// label_count(L): number of data vertices with label L (GFD_WILDCARD: all).
+// Returns GFD_OK or an error code (message set).
+int make_plan(const gfd_gfd* phi, int32_t n_attrs, const unsigned long long* label_stats,
+              int64_t n_vertices, HostPlan* out);
+
+}  // namespace gfd

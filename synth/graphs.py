@@ -65,7 +65,10 @@ def graph_from_edges(n_vertices, src, dst, elabel, vlabel, attrs, meta=None) -> 
     counts = np.bincount(s, minlength=n_vertices).astype(np.int64)
     off = np.zeros(n_vertices + 1, dtype=np.int64)
     np.cumsum(counts, out=off[1:])
-    attrs = np.ascontiguousarray(np.asarray(attrs, dtype=np.int32).reshape(-1, n_vertices))
+    attrs = np.asarray(attrs, dtype=np.int32)
+    if attrs.ndim != 2:
+        attrs = attrs.reshape(-1, n_vertices) if n_vertices else attrs.reshape(0, 0)
+    attrs = np.ascontiguousarray(attrs)
     return Graph(n_vertices, off, dst[order].astype(np.int32), elabel[order],
                  np.ascontiguousarray(np.asarray(vlabel, dtype=np.int32)), attrs,
                  meta or {})

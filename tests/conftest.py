@@ -18,3 +18,8 @@ def oracle_mod():
     from oracle import oracle
     oracle.build_oracle()
     return oracle
+
+
+# bound every device-side wait and every enumeration run in the tests
+os.environ.setdefault("GFD_WAIT_LIMIT_MS", "10000")
+os.environ.setdefault("GFD_RUN_LIMIT_MS", "120000")
