@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Benchmark: matches validated per second, batched vs per-GFD, on one GB300.
+
+A step validates the whole GFD batch of the workload against the resident
+graph through the C-ABI (gfd_validate_batch): candidate filter, refinement,
+index build, core-first enumeration and literal check, all in the library's
+CUDA kernels. `value` is whole-job matches/s with the graph already resident;
+`e2e` adds, every step, the host-side GFD descriptions going in and the sorted
+violation tuples coming back to host memory. `plain` times the same GFDs as
+one gfd_validate call each. `--impl reference` times the CPU oracle instead,
+on a bounded root sample of the same workload.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torch.distributed.run, one process per GPU, each validating its own replica of
+the workload (no data-path collective; the batch does not need one).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "matches validated/s, batched vs per-GFD; p50/p99 request latency (1 GB300)"
+UNIT = "matches/s"
+SRC_ENUM = os.path.join(ROOT, "paper_2608_02321_gb300", "csrc", "enumerate.cu")
+PROFILE_NOTE = os.path.join(ROOT, "profiles", "enumerate_batched.md")
+
+
+# ------------------------------------------------------------------ workloads
+def make_workload(name: str, scale: int):
+    from synth import configs
+    if name == "batched":
+        g, qs = configs.batched(scale=scale)
+        desc = (f"batched: {g.n_vertices} vertices, {g.n_edges} edges, 128 vertex labels Zipf(1.2), "
+                f"32 edge labels, 4 attributes Zipf(1.1); {len(qs)} GFDs of 3-8 nodes "
+                f"(tree/cycle/4-clique/triangle-with-tails), 0-3 X literals, 1 Y literal")
+    elif name == "mid":
+        g, qs = configs.mid(scale=scale)
+        desc = f"mid: {g.n_vertices} vertices, {g.n_edges} edges, one 5-node GFD"
+    elif name == "tiny":
+        g, qs = configs.tiny()
+        desc = f"tiny: {g.n_vertices} vertices, {g.n_edges} edges, one 3-node GFD, 50 planted violations"
+    elif name == "kg":
+        g, qs = configs.kg(scale=scale)
+        desc = f"kg: {g.n_vertices} vertices, {g.n_edges} edges, {len(qs)} 6-node GFDs"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return g, qs, desc
+
+
+def literal_attrs(q) -> int:
+    s = set()
+    for l in list(q.X) + list(q.Y):
+        s.add((l.x, l.a))
+        if l.kind == 1:
+            s.add((l.y, l.b))
+    return len(s)
+
+
+def gfd_bytes(q) -> int:
+    return 4 * q.k + 12 * len(q.edges) + 24 * (len(q.X) + len(q.Y)) + 64
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(g, qs, seconds: float, threads: int, seed: int = 7):
+    """Run the oracle over seeded random root samples of every GFD until about
+    `seconds` of wall time has passed; returns (matches, wall seconds, roots)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import oracle
+    og = oracle.OracleGraph(g)
+    rng = np.random.default_rng(seed)
+    # one task = (gfd, 64 random roots); tasks interleave the GFDs
+    tasks = []
+    per = 64
+    n_rounds = max(1, int(200000 // max(1, len(qs) * per)))
+    for r in range(n_rounds):
+        for i in range(len(qs)):
+            tasks.append((i, rng.integers(0, g.n_vertices, size=per).astype(np.int32)))
+    matches = 0
+    roots = 0
+    t0 = time.perf_counter()
+    lock = threading.Lock()
+    stop = threading.Event()
+
+    def run(task):
+        nonlocal matches, roots
+        if stop.is_set():
+            return
+        i, rs = task
+        nm, _ = oracle.validate(og, qs[i], roots=rs)
+        with lock:
+            matches += nm
+            roots += rs.shape[0]
+        if time.perf_counter() - t0 > seconds:
+            stop.set()
+
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(run, tasks))
+    return matches, time.perf_counter() - t0, roots
+
+
+def cpu_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, g, qs, desc):
+    """The oracle, as it stands, on the host cores: each step a bounded root sample."""
+    threads = cpu_threads()
+    per_step = max(2.0, args.cpu_seconds / 2)
+    for w in range(args.warmup):
+        oracle_sample(g, qs, per_step / 4, threads, seed=100 + w)
+    tot_m = tot_t = 0.0
+    tot_r = 0
+    for s in range(args.steps):
+        m, t, r = oracle_sample(g, qs, per_step, threads, seed=1000 + s)
+        tot_m += m
+        tot_t += t
+        tot_r += r
+    value = tot_m / tot_t if tot_t > 0 else 0.0
+    sample = (f"{tot_r} random root vertices (images of pattern node 0) spread over all "
+              f"{len(qs)} GFDs, about {per_step:.0f} s of oracle time per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": desc, "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def kernel_traffic():
+    """dram bytes per launch of the enumeration kernel from the committed ncu
+    summary, if it was taken on the current source of that kernel."""
+    try:
+        text = open(PROFILE_NOTE).read()
+    except OSError:
+        return None
+    sha = hashlib.sha256(open(SRC_ENUM, "rb").read()).hexdigest()[:16]
+    t = None
+    s = None
+    for ln in text.splitlines():
+        if ln.startswith("traffic_bytes_per_launch:"):
+            t = float(ln.split(":", 1)[1].split()[0])
+        if ln.startswith("source_sha256_16:"):
+            s = ln.split(":", 1)[1].strip()
+    return t if (t is not None and s == sha) else None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gfd", choices=["gfd", "reference"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "mid", "tiny", "kg"])
+    ap.add_argument("--scale", type=int, default=1, help="divide V and E (tests only)")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--flags", type=int, default=0)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        g, qs, desc = make_workload(args.workload, args.scale)
+        run_reference(args, g, qs, desc)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    import paper_2608_02321_gb300 as G
+    G.load_library(build_if_missing=False)
+    g, qs, desc = make_workload(args.workload, args.scale)
+    stream = torch.cuda.current_stream()
+    dg = G.Graph(g, stream=stream)
+    flags = G.FLAG_PROFILE | args.flags
+    hint = 1 << 20
+    l2_flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        return dg.validate_batch(qs, stream=stream, flags=flags, max_violations_hint=hint)
+
+    for _ in range(args.warmup):
+        res = step()
+        hint = max(hint, max(r.n_violations for r in res) + 1)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, enum_ms, enum_launches, launches = [], [], 0, 0
+    stats = None
+    for _ in range(args.steps):
+        l2_flush.zero_()
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        ms, nl = res[0].profile(G.PROF_ENUM)
+        enum_ms.append(ms)
+        enum_launches += 1
+        launches += sum(res[0].profile(w)[1] for w in range(4))
+        stats = res
+    clk = clocks.stop()
+    matches = sum(r.n_matches for r in stats)
+    viols = sum(r.n_violations for r in stats)
+    work = sum(r.stat(G.STAT_WORK) for r in stats)
+    rows = sum(r.stat(G.STAT_ROWS) for r in stats)
+    probes = stats[0].stat(G.STAT_PROBES)
+    step_ms = float(np.mean(times))
+    # max over ranks
+    t_local = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
+    m_local = torch.tensor([float(matches)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+        dist.all_reduce(m_local, op=dist.ReduceOp.SUM)
+    step_ms_max = float(t_local.item())
+    value = float(m_local.item()) / (step_ms_max / 1000.0)
+
+    # algorithmic bytes of one enumeration launch
+    lit_bytes = sum(r.n_matches * 32 * literal_attrs(q) for r, q in zip(stats, qs))
+    b_alg = 8 * work + 32 * probes + 8 * rows + lit_bytes + sum(4 * r.k * r.n_violations for r in stats)
+    t_enum = float(np.mean(enum_ms)) / 1000.0
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = b_alg / t_enum / 1e9 if t_enum > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if peak else None, "traffic": kernel_traffic(),
+                "kernel": "k_persistent (enumeration)", "launch_ms": t_enum * 1000,
+                "alg_bytes_per_launch": b_alg,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+    # e2e: host GFDs in, sorted violation tuples back on the host
+    e2e_times = []
+    d2h = 0
+    for _ in range(max(1, min(3, args.steps))):
+        l2_flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = step()
+        d2h = 0
+        for r in res:
+            v = r.violations()
+            d2h += v.nbytes + 16
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = float(np.mean(e2e_times))
+    e2e = {"value": matches / e2e_s, "unit": UNIT, "h2d_bytes_per_step": sum(gfd_bytes(q) for q in qs),
+           "d2h_bytes_per_step": d2h, "ms_per_step": 1000 * e2e_s,
+           "includes": "validate_batch from host GFDs + device sort and copy of all violation tuples"}
+
+    plain = None
+    if not args.no_plain and len(qs) > 1:
+        ptimes = []
+        for _ in range(max(1, min(2, args.steps))):
+            l2_flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pm = 0
+            for q in qs:
+                r = dg.validate(q, stream=stream, max_violations_hint=hint)
+                pm += r.n_matches
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ptimes.append(e0.elapsed_time(e1))
+        pms = float(np.mean(ptimes))
+        plain = {"value": pm / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms,
+                 "launch": f"{len(qs)} gfd_validate calls per step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = cpu_threads()
+        m, t, r = oracle_sample(g, qs, args.cpu_seconds, threads)
+        cpu = {"value": m / t if t > 0 else 0.0, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{r} random root vertices (images of pattern node 0) over all {len(qs)} GFDs, "
+                         f"{t:.1f} s wall"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": desc, "l2": "inputs larger than L2 and a 512 MB L2 flush before "
+                                                  "every timed step",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "plain": plain,
+                "batched_over_plain": (value / world) / plain["value"] if plain else None,
+                "matches_per_step": matches, "violations_per_step": viols,
+                "work_items_per_step": work, "edge_probes_per_step": probes}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

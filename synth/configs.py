@@ -91,9 +91,11 @@ MID_V, MID_E = 1_000_000, 8_000_000
 
 def mid_gfd() -> GFD:
     """Triangle x->y, y->z, x->z plus the pendant chain z->d->e (core {x,y,z},
-    forest d, leaf e), with x.A1 = 7 → y.A2 = z.A2."""
-    return GFD([0, 1, 2, 3, 4],
-               [(0, 1, 0), (1, 2, 1), (0, 2, 2), (2, 3, 3), (3, 4, 4)],
+    forest d, leaf e), with x.A1 = 7 → y.A2 = z.A2. Every node carries the most
+    frequent vertex label and the edges match any edge label: with 16 edge
+    labels, fixed edge labels leave almost no labelled triangles in this graph."""
+    return GFD([0, 0, 0, 0, 0],
+               [(0, 1, -1), (1, 2, -1), (0, 2, -1), (2, 3, -1), (3, 4, -1)],
                [Literal.const(0, 1, 7)], [Literal.var(1, 2, 2, 2)], False, "mid")
 
 
@@ -107,30 +109,54 @@ def mid(scale: int = 1) -> tuple[Graph, list[GFD]]:
 BATCH_V, BATCH_E, BATCH_N = 4_000_000, 40_000_000, 256
 
 
-def batched_gfds(n: int = BATCH_N, n_attrs: int = 4, seed_index: int = 2,
-                 vlabels=tuple(range(16)), elabels=tuple(range(8))) -> list[GFD]:
+BATCH_CAP = 1e8         # redraw a pattern whose expected match count exceeds this
+BATCH_TOP_LABELS = 8    # node labels among the most frequent ones
+BATCH_P_WILD_NODE = 0.25
+BATCH_P_WILD_EDGE = 0.75
+
+
+def batched_gfds(graph: Graph, n: int = BATCH_N, n_attrs: int = 4, n_elabels: int = 32,
+                 seed_index: int = 2) -> list[GFD]:
     """GFDs with k uniform in 3..8 (4..8 for the 4-clique), shape uniform over
-    tree / cycle / 4-clique / triangle-with-tails, labels from the 16 most frequent
-    vertex labels and 8 edge labels, 0-3 X literals and 1 Y literal; constants are
-    drawn from the attribute distribution."""
+    tree / cycle / 4-clique / triangle-with-tails, one randomly oriented edge per
+    skeleton pair. A node label is the wildcard with probability 1/4, else one
+    of the 8 most frequent vertex labels drawn in proportion to its frequency;
+    an edge label is the wildcard with probability 3/4, else uniform. X has 0-3
+    literals and Y one; each is constant or variable with equal odds, constants
+    drawn from the attribute distribution. A pattern whose expected match count
+    under the configuration model of the graph's degrees exceeds 1e8 is redrawn
+    (the paper's queries were chosen to have many embeddings, but bounded)."""
+    from .estimate import DegreeMoments
     rng = _rng(seed_index, 1)
+    dm = DegreeMoments(graph, n_elabels)
+    freq = np.bincount(graph.vlabel, minlength=BATCH_TOP_LABELS).astype(np.float64)
+    top = np.argsort(-freq, kind="stable")[:BATCH_TOP_LABELS]
+    p_top = freq[top] / max(1.0, freq[top].sum())
 
     def draw_const():
         return zipf_values(1, 1024, 1.1, rng)[0]
 
     out = []
     for i in range(n):
-        shape = SHAPES[int(rng.integers(0, 4))]
-        k = int(rng.integers(4 if shape == "clique4" else 3, 9))
-        out.append(random_pattern_gfd(rng, shape, k, vlabels, elabels, n_attrs, (0, 3), 1,
-                                      draw_const, name=f"b{i}_{shape}{k}"))
+        while True:
+            shape = SHAPES[int(rng.integers(0, 4))]
+            k = int(rng.integers(4 if shape == "clique4" else 3, 9))
+            q = random_pattern_gfd(rng, shape, k, [0], [0], n_attrs, (0, 3), 1, draw_const,
+                                   name=f"b{i}_{shape}{k}")
+            q.node_label = [-1 if rng.random() < BATCH_P_WILD_NODE else int(rng.choice(top, p=p_top))
+                            for _ in range(k)]
+            q.edges = [(a, b, -1 if rng.random() < BATCH_P_WILD_EDGE else int(rng.integers(0, n_elabels)))
+                       for (a, b, _) in q.edges]
+            if dm.expected_count(q) <= BATCH_CAP:
+                break
+        out.append(q)
     return out
 
 
 def batched(scale: int = 1, n_gfds: int = BATCH_N) -> tuple[Graph, list[GFD]]:
     g = powerlaw_graph(2, BATCH_V // scale, BATCH_E // scale, 128, 1.2, 32, 4, 1024, 1.1,
                        name="batched")
-    return g, batched_gfds(n_gfds)
+    return g, batched_gfds(g, n_gfds)
 
 
 # ------------------------------------------------------------- knowledge-graph

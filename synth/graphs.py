@@ -92,17 +92,42 @@ def powerlaw_weights(n: int, gamma: float, rng: np.random.Generator,
 
 
 def _sample(cdf: np.ndarray, m: int, rng: np.random.Generator) -> np.ndarray:
+    """m independent draws of index i with probability ∝ cdf[i] - cdf[i-1]."""
     u = rng.random(m) * cdf[-1]
     idx = np.searchsorted(cdf, u, side="right")
     np.minimum(idx, cdf.shape[0] - 1, out=idx)
     return idx
 
 
+def _sample_sorted(cdf: np.ndarray, m: int, rng: np.random.Generator) -> np.ndarray:
+    """The same distribution as _sample, returned in increasing order (sorted
+    uniforms make the inverse-CDF search cache friendly)."""
+    u = rng.random(m)
+    u.sort()
+    u *= cdf[-1]
+    # draws that fall in [cdf[i-1], cdf[i]) map to i
+    below = np.searchsorted(u, cdf, side="left")
+    counts = np.diff(below, prepend=0)
+    counts[-1] += m - below[-1]
+    return np.repeat(np.arange(cdf.shape[0], dtype=np.int64), counts)
+
+
+def _sorted_unique(a: np.ndarray) -> np.ndarray:
+    a.sort()
+    if a.shape[0] == 0:
+        return a
+    keep = np.empty(a.shape[0], dtype=bool)
+    keep[0] = True
+    np.not_equal(a[1:], a[:-1], out=keep[1:])
+    return a[keep]
+
+
 def chung_lu_edges(n: int, m: int, rng: np.random.Generator, gamma_out: float = 2.5,
                    gamma_in: float = 2.5, out_cap_frac: float | None = None):
-    """Directed Chung-Lu: sources drawn ∝ out-weight, destinations ∝ in-weight;
-    self-loops and repeated pairs are rejected until exactly m distinct edges
-    exist (the first m distinct pairs in sampling order are kept)."""
+    """Directed Chung-Lu: each candidate edge draws its source ∝ out-weight and
+    its destination ∝ in-weight independently; self-loops and repeated pairs are
+    dropped, more candidates are drawn until at least m distinct pairs exist,
+    and a seeded uniform random subset of exactly m of them is kept."""
     if m > n * (n - 1):
         raise ValueError("too many edges")
     w_out = powerlaw_weights(n, gamma_out, rng, out_cap_frac)
@@ -113,19 +138,18 @@ def chung_lu_edges(n: int, m: int, rng: np.random.Generator, gamma_out: float = 
     need = m
     while True:
         batch = int(need * 1.15) + 1024
-        s = _sample(cdf_out, batch, rng)
-        d = _sample(cdf_in, batch, rng)
+        s = _sample_sorted(cdf_out, batch, rng)[rng.permutation(batch)]   # random pairing
+        d = _sample_sorted(cdf_in, batch, rng)
         k = s.astype(np.int64) * n + d
-        k = k[s != d]
-        keys = np.concatenate([keys, k])
-        _, first = np.unique(keys, return_index=True)
-        if first.shape[0] >= m:
-            first.sort()
-            keys = keys[first[:m]]
+        keys = _sorted_unique(np.concatenate([keys, k[s != d]]))
+        if keys.shape[0] >= m:
             break
-        first.sort()
-        keys = keys[first]
         need = m - keys.shape[0]
+    if keys.shape[0] > m:
+        drop = rng.choice(keys.shape[0], keys.shape[0] - m, replace=False)
+        mask = np.ones(keys.shape[0], dtype=bool)
+        mask[drop] = False
+        keys = keys[mask]
     return keys // n, keys % n
 
 

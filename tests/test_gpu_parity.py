@@ -3,6 +3,7 @@ match counts and identical sorted violation lists (integer work: bit-exact)."""
 from __future__ import annotations
 
 import math
+import os
 
 import numpy as np
 import pytest
@@ -128,29 +129,42 @@ def test_tiny_workload(lib, oracle_mod):
         assert_same(gpu_run(dg, qs[0], flags=flags), want, f"tiny flags={flags}")
 
 
-def test_mid_workload_scaled(lib, oracle_mod):
-    """The mid workload's structure at 1/20 of its size, exact."""
-    g, qs = configs.mid(scale=20)
-    want = oracle_mod.validate(g, qs[0], threads=8)
-    assert_same(gpu_run(gpu_graph(g), qs[0]), want, "mid/20")
+def test_mid_workload(lib, oracle_mod):
+    """The mid workload at full size (1M vertices, 8M edges), exact."""
+    g, qs = configs.mid()
+    want = oracle_mod.validate(g, qs[0], threads=os.cpu_count() or 8)
+    assert want[0] > 10000 and want[1].shape[0] > 0
+    dg = gpu_graph(g)
+    assert_same(gpu_run(dg, qs[0]), want, "mid")
+    assert_same(gpu_run(dg, qs[0], flags=G.FLAG_HOST_LOOP, chunk_rows=4096), want, "mid small chunks")
 
 
-def test_batched_workload_scaled_equals_single(lib, oracle_mod):
-    """64 GFDs of the batched recipe on a 1/200 graph: the batch equals the
-    oracle and equals one-at-a-time validation."""
-    g, _ = configs.batched(scale=200)
-    qs = configs.batched_gfds(64)
+def _batched_vs_oracle(oracle_mod, scale, n):
+    g, qs = configs.batched(scale=scale, n_gfds=n)
     dg = gpu_graph(g)
     res = dg.validate_batch(qs)
     og = oracle_mod.OracleGraph(g)
-    total = 0
+    total = nonzero = 0
     for i, q in enumerate(qs):
-        want = oracle_mod.validate(og, q)
-        assert_same((res[i].n_matches, res[i].violations()), want, f"batch gfd {i}")
+        want = oracle_mod.validate(og, q, threads=os.cpu_count() or 8)
+        assert_same((res[i].n_matches, res[i].violations()), want, f"batch gfd {i} {q.name}")
         total += want[0]
+        nonzero += want[0] > 0
         if i % 8 == 0:
             assert_same(gpu_run(dg, q), want, f"single gfd {i}")
-    assert total > 0
+    assert total > 100000 and nonzero > n // 3
+
+
+def test_batched_workload_scaled(lib, oracle_mod):
+    """The first 64 GFDs of the batched recipe on a 1/400 graph (10K vertices,
+    100K edges): the batch equals the oracle and one-at-a-time validation."""
+    _batched_vs_oracle(oracle_mod, 400, 64)
+
+
+@pytest.mark.slow
+def test_batched_workload_scaled_all(lib, oracle_mod):
+    """All 256 GFDs of the batched recipe on the 1/400 graph."""
+    _batched_vs_oracle(oracle_mod, 400, 256)
 
 
 def test_violation_capacity_regrows(lib, oracle_mod):
