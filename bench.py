@@ -271,7 +271,6 @@ def main():
 
     for _ in range(args.warmup):
         res = step()
-        hint = max(hint, max(r.n_violations for r in res) + 1)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
@@ -385,7 +384,9 @@ def main():
                 "clocks": clk, "plain": plain,
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,
                 "matches_per_step": matches, "violations_per_step": viols,
-                "work_items_per_step": work, "edge_probes_per_step": probes}
+                "work_items_per_step": work, "edge_probes_per_step": probes,
+                "gfds_rerun_for_violation_capacity": sum(r.stat(G.STAT_RERUN) for r in stats),
+                "step_ms_all": times, "enum_ms_all": enum_ms}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -178,8 +178,9 @@ const int32_t *gfd_result_tuples(gfd_result *r);
  * number of launches, when GFD_FLAG_PROFILE was set; else 0. */
 double gfd_result_profile(const gfd_result *r, int32_t which, int64_t *launches);
 /* Statistics of the run: 0 supersteps, 1 work items expanded, 2 partial
- * matches written, 3 edge-lookup probes, 4 candidate-list entries (sum over
- * pattern nodes), 5 index entries. */
+ * matches written, 3 edge-lookup probes (whole run), 4 candidate-list entries
+ * (sum over pattern nodes), 5 index entries, 6 number of extra runs made
+ * because the violations outgrew max_violations_hint. */
 uint64_t gfd_result_stat(const gfd_result *r, int32_t which);
 /* Release a result. */
 void gfd_result_free(gfd_result *r);

@@ -33,7 +33,7 @@ FLAG_PROFILE = 0x4
 FLAG_NO_GRAPH = 0x8
 
 PROF_FILTER, PROF_REFINE, PROF_INDEX, PROF_ENUM, PROF_SORT = range(5)
-STAT_STEPS, STAT_WORK, STAT_ROWS, STAT_PROBES, STAT_CANDIDATES, STAT_INDEX = range(6)
+STAT_STEPS, STAT_WORK, STAT_ROWS, STAT_PROBES, STAT_CANDIDATES, STAT_INDEX, STAT_RERUN = range(7)
 
 
 class GfdError(RuntimeError):

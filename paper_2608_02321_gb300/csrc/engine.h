@@ -35,7 +35,7 @@ struct gfd_result {
     std::vector<int32_t> tuples;
     double prof_ms[5] = {0, 0, 0, 0, 0};
     int64_t prof_launch[5] = {0, 0, 0, 0, 0};
-    uint64_t stat[6] = {0, 0, 0, 0, 0, 0};
+    uint64_t stat[7] = {0, 0, 0, 0, 0, 0, 0};
     cudaStream_t stream = nullptr;
 };
 

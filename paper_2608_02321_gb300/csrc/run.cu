@@ -551,6 +551,7 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
     for (int s = 0; s < n; s++) {
         if (redo_res[s]) {
             out[s] = redo_res[s];
+            out[s]->stat[6] += 1;
             cudaFreeAsync(vbuf[s], st);
             vbuf[s] = nullptr;
             continue;
