@@ -185,6 +185,26 @@ uint64_t gfd_result_stat(const gfd_result *r, int32_t which);
 /* Release a result. */
 void gfd_result_free(gfd_result *r);
 
+/* Candidate filter of pattern node `node` of phi (its label, its out- and
+ * in-degree in Q as lower bounds on the data vertex's degrees without
+ * self-loops, and its self-loop), written to the caller's DEVICE buffer d_out as
+ * increasing vertex ids; *n_out (host) receives how many there are. It
+ * allocates no device memory, for callers that must not: code running while a
+ * stream is captured into a CUDA graph, servers whose device memory belongs to
+ * another allocator or a fixed budget, threads that cannot take the
+ * device-wide synchronisation of cudaMalloc/cudaFree. The paper has no
+ * counterpart; the same filter runs inside gfd_validate. Its only scratch is a
+ * fixed 64 KiB array inside the library, so graphs are limited to 2^26
+ * vertices (GFD_ERR_UNSUPPORTED beyond). The first call on each device looks
+ * that array up (make it before any stream capture). All calls share the
+ * array: calls that overlap on the GPU race, so serialize them (one stream, or
+ * wait for the previous call). out_cap is the capacity of d_out in elements;
+ * more candidates than that give GFD_ERR_OVERFLOW with *n_out set. The call
+ * waits for its own work on cuda_stream (NULL: the graph's stream). */
+int gfd_node_candidates_noalloc(const gfd_graph *g, const gfd_gfd *phi, int32_t node,
+                                int32_t *d_out, int64_t out_cap, int64_t *n_out,
+                                void *cuda_stream);
+
 /* Message for the calling thread's last non-OK return ("" if none). */
 const char *gfd_last_error(void);
 

@@ -84,6 +84,8 @@ _SIGS = {
     "gfd_result_profile": (C.c_double, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
     "gfd_result_stat": (C.c_uint64, [C.c_void_p, C.c_int32]),
     "gfd_result_free": (None, [C.c_void_p]),
+    "gfd_node_candidates_noalloc": (C.c_int, [C.c_void_p, C.POINTER(gfd_gfd), C.c_int32, C.c_void_p,
+                                              C.c_int64, C.POINTER(C.c_int64), C.c_void_p]),
     "gfd_last_error": (C.c_char_p, []),
 }
 
@@ -279,6 +281,17 @@ class Graph:
         outs = (C.c_void_p * max(1, len(bufs)))()
         _check(_lib.gfd_validate_batch(self._h, arr, len(bufs), C.byref(o), outs))
         return [Result(C.c_void_p(outs[i])) for i in range(len(bufs))]
+
+
+def node_candidates_noalloc(g: Graph, gfd, node: int, out_ptr: int, out_cap: int, stream=None) -> int:
+    """Candidate vertices of pattern node `node` written to the caller's device
+    buffer at out_ptr (int32, out_cap elements) without any device allocation by
+    the library; returns their number. See include/gfd.h for the limits."""
+    b = _GfdBuf(gfd)
+    n = C.c_int64(0)
+    _check(_lib.gfd_node_candidates_noalloc(g._h, C.byref(b.s), int(node), out_ptr, int(out_cap),
+                                            C.byref(n), _stream_handle(stream)))
+    return int(n.value)
 
 
 def graph_load(graph, stream=None, with_reverse: bool = False) -> Graph:
