@@ -133,40 +133,30 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle
 def oracle_sample(g, qs, seconds: float, threads: int, seed: int = 7):
-    """Run the oracle over seeded random root samples of every GFD until about
-    `seconds` of wall time has passed; returns (matches, wall seconds, roots)."""
+    """The oracle over seeded random root samples of every GFD for about
+    `seconds` of wall time on `threads` host threads; the root in progress at
+    the deadline is dropped. Returns (matches, wall seconds, roots searched)."""
     from concurrent.futures import ThreadPoolExecutor
     from oracle import oracle
     og = oracle.OracleGraph(g)
     rng = np.random.default_rng(seed)
-    # one task = (gfd, 64 random roots); tasks interleave the GFDs
-    tasks = []
-    per = 64
-    n_rounds = max(1, int(200000 // max(1, len(qs) * per)))
-    for r in range(n_rounds):
-        for i in range(len(qs)):
-            tasks.append((i, rng.integers(0, g.n_vertices, size=per).astype(np.int32)))
-    matches = 0
-    roots = 0
+    per = 16
+    tasks = [(i, rng.integers(0, g.n_vertices, size=per).astype(np.int32))
+             for _ in range(max(1, 100000 // max(1, len(qs) * per))) for i in range(len(qs))]
     t0 = time.perf_counter()
-    lock = threading.Lock()
-    stop = threading.Event()
+    deadline = t0 + seconds
 
     def run(task):
-        nonlocal matches, roots
-        if stop.is_set():
-            return
+        left = deadline - time.perf_counter()
+        if left <= 0:
+            return 0, 0
         i, rs = task
-        nm, _ = oracle.validate(og, qs[i], roots=rs)
-        with lock:
-            matches += nm
-            roots += rs.shape[0]
-        if time.perf_counter() - t0 > seconds:
-            stop.set()
+        return oracle.count_within(og, qs[i], rs, left)
 
     with ThreadPoolExecutor(threads) as ex:
-        list(ex.map(run, tasks))
-    return matches, time.perf_counter() - t0, roots
+        res = list(ex.map(run, tasks))
+    wall = time.perf_counter() - t0
+    return sum(r[0] for r in res), wall, sum(r[1] for r in res)
 
 
 def cpu_threads() -> int:

@@ -29,9 +29,11 @@
  * placed before it. Edge lookup is a binary search in the oracle's own sorted
  * copy of the adjacency.
  */
+#define _POSIX_C_SOURCE 200809L
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 
 #define OG_ABSENT INT32_MIN
 #define OG_NOEDGE (-2)
@@ -156,7 +158,16 @@ typedef struct {
     int32_t h[OG_MAXK];                /* h[node] = vertex */
     uint64_t n_matches;
     int32_t *viol; int64_t n_viol, cap_viol;
+    double deadline;                   /* monotonic seconds; 0 = none */
+    uint64_t calls;
+    int aborted;
 } og_state;
+
+static double og_now(void) {
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
 
 static int og_label_ok(int32_t want, int32_t have) {
     return want == OG_WILDCARD || want == have;
@@ -229,6 +240,11 @@ static void og_extend(og_state *s, int i) {
     else            { a = g->in_off[hp];  b = g->in_off[hp + 1]; }
     for (e = a; e < b; e++) {
         int32_t v = s->pout[i] ? g->out_nbr[e] : g->in_nbr[e];
+        if (s->aborted) return;
+        if (s->deadline > 0 && (++s->calls & 0xfff) == 0 && og_now() > s->deadline) {
+            s->aborted = 1;
+            return;
+        }
         if (!og_candidate_ok(s, i, v)) continue;
         s->h[u] = v;
         og_extend(s, i + 1);
@@ -236,10 +252,14 @@ static void og_extend(og_state *s, int i) {
 }
 
 /* Validate one GFD. roots: the vertices tried for pattern node 0 (NULL: all of V).
+ * seconds > 0 bounds the run: the root being searched when time runs out is
+ * dropped together with its matches, and *roots_done tells how many roots were
+ * searched to the end (all of them when there is no bound).
  * Returns 0 on success, 1 for a malformed or disconnected pattern. On success the
  * caller owns *viol_out (free with og_free). */
-int og_validate(const og_graph *g, const og_gfd *q, const int32_t *roots, int64_t n_roots,
-                uint64_t *n_matches, int32_t **viol_out, int64_t *n_viol) {
+int og_validate_budget(const og_graph *g, const og_gfd *q, const int32_t *roots, int64_t n_roots,
+                       double seconds, uint64_t *n_matches, int32_t **viol_out, int64_t *n_viol,
+                       int64_t *roots_done) {
     og_state s;
     int32_t placed[OG_MAXK];
     int i, j, head, tail;
@@ -283,17 +303,31 @@ int og_validate(const og_graph *g, const og_gfd *q, const int32_t *roots, int64_
             if (s.qedge[u][w] != OG_NOEDGE) { s.pnode[i] = w; s.pout[i] = 0; break; }
         }
     }
+    s.deadline = seconds > 0 ? og_now() + seconds : 0;
     for (r = 0; r < (roots ? n_roots : (int64_t)g->n); r++) {
         int32_t v = roots ? roots[r] : (int32_t)r;
+        uint64_t m0 = s.n_matches;
+        int64_t v0 = s.n_viol;
         if (v < 0 || v >= g->n) continue;
         if (!og_candidate_ok(&s, 0, v)) continue;
         s.h[0] = v;
         og_extend(&s, 1);
+        if (s.aborted) {          /* drop the unfinished root */
+            s.n_matches = m0;
+            s.n_viol = v0;
+            break;
+        }
     }
+    if (roots_done) *roots_done = r;
     *n_matches = s.n_matches;
     *viol_out = s.viol;
     *n_viol = s.n_viol;
     return 0;
+}
+
+int og_validate(const og_graph *g, const og_gfd *q, const int32_t *roots, int64_t n_roots,
+                uint64_t *n_matches, int32_t **viol_out, int64_t *n_viol) {
+    return og_validate_budget(g, q, roots, n_roots, 0.0, n_matches, viol_out, n_viol, NULL);
 }
 
 /* --------------------------------------------------------------- sorting */

@@ -60,6 +60,10 @@ def bind_library(path: str):
     lib.og_validate.argtypes = [C.c_void_p, C.POINTER(_Gfd), C.c_void_p, C.c_int64,
                                 C.POINTER(C.c_uint64), C.POINTER(C.c_void_p),
                                 C.POINTER(C.c_int64)]
+    lib.og_validate_budget.restype = C.c_int
+    lib.og_validate_budget.argtypes = [C.c_void_p, C.POINTER(_Gfd), C.c_void_p, C.c_int64, C.c_double,
+                                       C.POINTER(C.c_uint64), C.POINTER(C.c_void_p),
+                                       C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     lib.og_free.argtypes = [C.c_void_p]
     return lib
 
@@ -161,6 +165,26 @@ def _run(og: OracleGraph, gfd, roots):
         lib.og_free(vp)
     del keep
     return int(nm.value), out
+
+
+def count_within(og: OracleGraph, gfd, roots, seconds: float):
+    """(matches, roots searched to the end) for the given roots, stopping after
+    about `seconds`; the root in progress at the deadline is not counted."""
+    lib = og._lib
+    s, keep = _gfd_struct(gfd)
+    nm = C.c_uint64(0)
+    vp = C.c_void_p(None)
+    nv = C.c_int64(0)
+    done = C.c_int64(0)
+    r = np.ascontiguousarray(roots, dtype=np.int32)
+    rc = lib.og_validate_budget(og._h, C.byref(s), _ptr(r), int(r.shape[0]), float(seconds), C.byref(nm),
+                                C.byref(vp), C.byref(nv), C.byref(done))
+    if vp.value:
+        lib.og_free(vp)
+    del keep
+    if rc != 0:
+        raise ValueError("oracle rejected the GFD (malformed or disconnected pattern)")
+    return int(nm.value), int(done.value)
 
 
 def sort_tuples(t: np.ndarray) -> np.ndarray:

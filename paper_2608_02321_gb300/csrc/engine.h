@@ -53,6 +53,7 @@ struct CompactJob {      // rank and candidate list of bm
     uint32_t* rank;
     int32_t* cand;
     uint32_t* count;
+    uint32_t* csum;          // per-chunk set-bit counts (scratch)
 };
 struct ScatterJob {      // mark vertices adjacent to the candidates of another level
     const int32_t* qcand;
@@ -82,6 +83,7 @@ struct CpiJob {          // index edges of one spanning-tree edge
     int32_t out;             // 1: children are out-neighbours of the parent candidates
     int32_t lab;
     uint64_t* nnz_stat;
+    uint64_t* csum;          // per-chunk count sums (scratch)
 };
 
 // ---- index kernels (index.cu); each launch covers all jobs given
@@ -90,7 +92,10 @@ int launch_and(const DevGraph& g, const AndJob* d_jobs, int njobs, cudaStream_t 
 int launch_compact(const DevGraph& g, const CompactJob* d_jobs, int njobs, cudaStream_t st);
 int launch_scatter(const DevGraph& g, const ScatterJob* d_jobs, int njobs, cudaStream_t st);
 int launch_prune(const DevGraph& g, const PruneJob* d_jobs, int njobs, cudaStream_t st);
-int launch_cpi(const DevGraph& g, const CpiJob* d_jobs, int njobs, int32_t* d_err, cudaStream_t st);
+int launch_cpi(const DevGraph& g, const CpiJob* d_jobs, int njobs, uint32_t nchunks, int32_t* d_err,
+               cudaStream_t st);
+uint32_t compact_chunks(const DevGraph& g);
+uint32_t cpi_chunks(uint64_t max_parent_candidates);
 
 // ---- enumeration (enumerate.cu)
 struct EnumArgs {

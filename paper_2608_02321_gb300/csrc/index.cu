@@ -23,6 +23,7 @@ namespace {
 
 constexpr int FILTER_THREADS = 256;
 constexpr int COMPACT_THREADS = 1024;
+constexpr uint32_t COMPACT_WORDS = 4096;  // words (or counts) per chunk
 constexpr int WARP_KERNEL_THREADS = 256;
 
 __device__ __forceinline__ uint64_t gwarp_id() {
@@ -78,33 +79,66 @@ __global__ void k_and(DevGraph g, const AndJob* __restrict__ jobs, int njobs) {
     }
 }
 
-// One block per job: rank[w] = number of set bits before word w; cand = the
-// set bits in increasing order; *count = total.
-__global__ void __launch_bounds__(COMPACT_THREADS) k_compact(DevGraph g, const CompactJob* __restrict__ jobs, int njobs) {
+// Compaction in two passes over (job, chunk) items so that even one job uses
+// the whole GPU: k_compact_sums counts set bits per chunk of COMPACT_WORDS
+// words; k_compact_write adds the counts of the preceding chunks, scans its own
+// chunk and writes rank[w] (set bits before word w) and the candidate list.
+__global__ void __launch_bounds__(COMPACT_THREADS) k_compact_sums(DevGraph g, const CompactJob* __restrict__ jobs,
+                                                                  int njobs, uint32_t nchunks) {
+    using Reduce = cub::BlockReduce<uint32_t, COMPACT_THREADS>;
+    __shared__ typename Reduce::TempStorage tmp;
+    for (uint64_t it = blockIdx.x; it < (uint64_t)njobs * nchunks; it += gridDim.x) {
+        const CompactJob& J = jobs[it / nchunks];
+        const uint32_t c = (uint32_t)(it % nchunks);
+        uint32_t cnt = 0;
+        for (uint32_t w = c * COMPACT_WORDS + threadIdx.x; w < min(g.nwords, (c + 1) * COMPACT_WORDS);
+             w += COMPACT_THREADS)
+            cnt += __popc(J.bm[w]);
+        cnt = Reduce(tmp).Sum(cnt);
+        if (threadIdx.x == 0) J.csum[c] = cnt;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(COMPACT_THREADS) k_compact_write(DevGraph g, const CompactJob* __restrict__ jobs,
+                                                                   int njobs, uint32_t nchunks) {
     using Scan = cub::BlockScan<uint32_t, COMPACT_THREADS>;
-    __shared__ typename Scan::TempStorage tmp;
-    for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
-        const CompactJob J = jobs[j];
-        uint32_t carry = 0;
-        for (uint32_t base = 0; base < g.nwords; base += COMPACT_THREADS) {
-            const uint32_t w = base + threadIdx.x;
-            const uint32_t word = w < g.nwords ? J.bm[w] : 0u;
-            uint32_t excl, total;
-            Scan(tmp).ExclusiveSum((uint32_t)__popc(word), excl, total);
-            if (w < g.nwords) {
-                const uint32_t r = carry + excl;
-                J.rank[w] = r;
-                uint32_t x = word, o = r;
-                while (x) {
-                    const int b = __ffs(x) - 1;
-                    J.cand[o++] = (int32_t)(w * 32 + b);
-                    x &= x - 1;
-                }
-            }
-            carry += total;
-            __syncthreads();
+    using Reduce = cub::BlockReduce<uint32_t, COMPACT_THREADS>;
+    __shared__ union {
+        typename Scan::TempStorage scan;
+        typename Reduce::TempStorage reduce;
+    } tmp;
+    __shared__ uint32_t base_s;
+    constexpr int WPT = COMPACT_WORDS / COMPACT_THREADS;  // words per thread
+    for (uint64_t it = blockIdx.x; it < (uint64_t)njobs * nchunks; it += gridDim.x) {
+        const CompactJob& J = jobs[it / nchunks];
+        const uint32_t c = (uint32_t)(it % nchunks);
+        uint32_t before = 0;
+        for (uint32_t q = threadIdx.x; q < c; q += COMPACT_THREADS) before += J.csum[q];
+        before = Reduce(tmp.reduce).Sum(before);
+        if (threadIdx.x == 0) base_s = before;
+        __syncthreads();
+        const uint32_t w0 = c * COMPACT_WORDS + threadIdx.x * WPT;
+        uint32_t words[WPT];
+        uint32_t cnt = 0;
+        for (int q = 0; q < WPT; q++) {
+            words[q] = w0 + q < g.nwords ? J.bm[w0 + q] : 0u;
+            cnt += __popc(words[q]);
         }
-        if (threadIdx.x == 0) *J.count = carry;
+        uint32_t excl, total;
+        Scan(tmp.scan).ExclusiveSum(cnt, excl, total);
+        uint32_t r = base_s + excl;
+        for (int q = 0; q < WPT; q++) {
+            if (w0 + q >= g.nwords) break;
+            J.rank[w0 + q] = r;
+            uint32_t x = words[q];
+            while (x) {
+                const int bpos = __ffs(x) - 1;
+                J.cand[r++] = (int32_t)((w0 + q) * 32 + bpos);
+                x &= x - 1;
+            }
+        }
+        if (c == nchunks - 1 && threadIdx.x == 0) *J.count = base_s + total;
         __syncthreads();
     }
 }
@@ -186,30 +220,71 @@ __global__ void k_cpi_count(DevGraph g, const CpiJob* __restrict__ jobs, int njo
     }
 }
 
-// One block per job: exclusive scan of off[0..n), off[n] = total.
-__global__ void __launch_bounds__(COMPACT_THREADS) k_cpi_scan(const CpiJob* __restrict__ jobs, int njobs, int32_t* err) {
-    using Scan = cub::BlockScan<uint64_t, COMPACT_THREADS>;
-    __shared__ typename Scan::TempStorage tmp;
-    for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
-        const CpiJob J = jobs[j];
+// Exclusive scan of the per-candidate counts off[0..n) in place, off[n] =
+// total, in two passes over (job, chunk) items like the compaction above.
+__global__ void __launch_bounds__(COMPACT_THREADS) k_cpi_sums(const CpiJob* __restrict__ jobs, int njobs,
+                                                              uint32_t nchunks) {
+    using Reduce = cub::BlockReduce<uint64_t, COMPACT_THREADS>;
+    __shared__ typename Reduce::TempStorage tmp;
+    for (uint64_t it = blockIdx.x; it < (uint64_t)njobs * nchunks; it += gridDim.x) {
+        const CpiJob& J = jobs[it / nchunks];
+        const uint32_t c = (uint32_t)(it % nchunks);
         const uint32_t n = *J.pcount;
-        uint64_t carry = 0;
-        for (uint32_t base = 0; base < n; base += COMPACT_THREADS) {
-            const uint32_t a = base + threadIdx.x;
-            const uint64_t c = a < n ? J.off[a] : 0;
-            uint64_t excl, total;
-            Scan(tmp).ExclusiveSum(c, excl, total);
-            if (a < n) J.off[a] = (uint32_t)(carry + excl);
-            carry += total;
-            __syncthreads();
+        if ((uint64_t)c * COMPACT_WORDS >= n && c > 0) continue;
+        uint64_t cnt = 0;
+        for (uint32_t a = c * COMPACT_WORDS + threadIdx.x; a < min(n, (c + 1) * COMPACT_WORDS); a += COMPACT_THREADS)
+            cnt += J.off[a];
+        cnt = Reduce(tmp).Sum(cnt);
+        if (threadIdx.x == 0) J.csum[c] = cnt;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(COMPACT_THREADS) k_cpi_scan(const CpiJob* __restrict__ jobs, int njobs,
+                                                              uint32_t nchunks, int32_t* err) {
+    using Scan = cub::BlockScan<uint64_t, COMPACT_THREADS>;
+    using Reduce = cub::BlockReduce<uint64_t, COMPACT_THREADS>;
+    __shared__ union {
+        typename Scan::TempStorage scan;
+        typename Reduce::TempStorage reduce;
+    } tmp;
+    __shared__ uint64_t base_s;
+    constexpr int EPT = COMPACT_WORDS / COMPACT_THREADS;
+    for (uint64_t it = blockIdx.x; it < (uint64_t)njobs * nchunks; it += gridDim.x) {
+        const CpiJob& J = jobs[it / nchunks];
+        const uint32_t c = (uint32_t)(it % nchunks);
+        const uint32_t n = *J.pcount;
+        const uint32_t last = n / COMPACT_WORDS;  // chunk holding off[n]
+        if (c > last) continue;
+        uint64_t before = 0;
+        for (uint32_t q = threadIdx.x; q < c; q += COMPACT_THREADS) before += J.csum[q];
+        before = Reduce(tmp.reduce).Sum(before);
+        if (threadIdx.x == 0) base_s = before;
+        __syncthreads();
+        const uint32_t a0 = c * COMPACT_WORDS + threadIdx.x * EPT;
+        uint32_t vals[EPT];
+        uint64_t cnt = 0;
+        for (int q = 0; q < EPT; q++) {
+            vals[q] = a0 + q < n ? J.off[a0 + q] : 0u;
+            cnt += vals[q];
         }
-        if (threadIdx.x == 0) {
-            if (carry > J.cap || carry > 0xffffffffull) {
+        uint64_t excl, total;
+        Scan(tmp.scan).ExclusiveSum(cnt, excl, total);
+        uint64_t r = base_s + excl;
+        const bool overflow = base_s + total > J.cap || base_s + total > 0xffffffffull;
+        for (int q = 0; q < EPT; q++) {
+            if (a0 + q >= n) break;
+            J.off[a0 + q] = overflow ? 0u : (uint32_t)r;
+            r += vals[q];
+        }
+        if (c == last && threadIdx.x == 0) {
+            uint64_t tot = base_s + total;
+            if (overflow) {
                 atomicExch(err, DERR_CAPACITY);
-                carry = 0;  // leave an empty, consistent index
+                tot = 0;  // leave an empty index
             }
-            J.off[n] = (uint32_t)carry;
-            if (J.nnz_stat) atomicAdd((unsigned long long*)J.nnz_stat, (unsigned long long)carry);
+            J.off[n] = (uint32_t)tot;
+            if (J.nnz_stat) atomicAdd((unsigned long long*)J.nnz_stat, (unsigned long long)tot);
         }
         __syncthreads();
     }
@@ -278,9 +353,16 @@ int launch_and(const DevGraph& g, const AndJob* d_jobs, int njobs, cudaStream_t 
     return check_launch("k_and");
 }
 
+uint32_t compact_chunks(const DevGraph& g) {
+    return std::max<uint32_t>(1, (g.nwords + COMPACT_WORDS - 1) / COMPACT_WORDS);
+}
+
 int launch_compact(const DevGraph& g, const CompactJob* d_jobs, int njobs, cudaStream_t st) {
     if (njobs <= 0) return GFD_OK;
-    k_compact<<<std::min(njobs, 152 * 2), COMPACT_THREADS, 0, st>>>(g, d_jobs, njobs);
+    const uint32_t nch = compact_chunks(g);
+    const int grid = (int)std::min<uint64_t>((uint64_t)njobs * nch, 152 * 2);
+    k_compact_sums<<<grid, COMPACT_THREADS, 0, st>>>(g, d_jobs, njobs, nch);
+    k_compact_write<<<grid, COMPACT_THREADS, 0, st>>>(g, d_jobs, njobs, nch);
     return check_launch("k_compact");
 }
 
@@ -296,10 +378,17 @@ int launch_prune(const DevGraph& g, const PruneJob* d_jobs, int njobs, cudaStrea
     return check_launch("k_prune");
 }
 
-int launch_cpi(const DevGraph& g, const CpiJob* d_jobs, int njobs, int32_t* d_err, cudaStream_t st) {
+uint32_t cpi_chunks(uint64_t max_parent_candidates) {
+    return (uint32_t)(max_parent_candidates / COMPACT_WORDS + 1);
+}
+
+int launch_cpi(const DevGraph& g, const CpiJob* d_jobs, int njobs, uint32_t nchunks, int32_t* d_err,
+               cudaStream_t st) {
     if (njobs <= 0) return GFD_OK;
     k_cpi_count<<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs);
-    k_cpi_scan<<<std::min(njobs, 152 * 2), COMPACT_THREADS, 0, st>>>(d_jobs, njobs, d_err);
+    const int grid = (int)std::min<uint64_t>((uint64_t)njobs * nchunks, 152 * 4);
+    k_cpi_sums<<<grid, COMPACT_THREADS, 0, st>>>(d_jobs, njobs, nchunks);
+    k_cpi_scan<<<grid, COMPACT_THREADS, 0, st>>>(d_jobs, njobs, nchunks, d_err);
     k_cpi_fill<<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs);
     return check_launch("k_cpi");
 }

@@ -211,6 +211,28 @@ int make_plan(const gfd_gfd* phi, int32_t n_attrs, const unsigned long long* lab
                 n++;
             }
         }
+        // Required edges first: a candidate usually fails there, after one
+        // probe, before the absent-edge checks that almost always pass.
+        {
+            int8_t q2[2 * MAXK], d2[2 * MAXK];
+            int16_t e2[2 * MAXK];
+            int m2 = 0;
+            for (int pass = 0; pass < 2; pass++)
+                for (int c = 0; c < n; c++) {
+                    const bool required = L.chk_exp[c] != EXP_NONE;
+                    if (required == (pass == 0)) {
+                        q2[m2] = L.chk_q[c];
+                        d2[m2] = L.chk_dir[c];
+                        e2[m2] = L.chk_exp[c];
+                        m2++;
+                    }
+                }
+            for (int c = 0; c < n; c++) {
+                L.chk_q[c] = q2[c];
+                L.chk_dir[c] = d2[c];
+                L.chk_exp[c] = e2[c];
+            }
+        }
         L.nchk = (int8_t)n;
         // candidate filter key (degrees without self-loops)
         FilterKey& K = P->key[i];

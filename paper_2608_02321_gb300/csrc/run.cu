@@ -151,7 +151,7 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
     if (!budget) {
         size_t fr = 0, tot = 0;
         GFD_CUDA(cudaMemGetInfo(&fr, &tot));
-        budget = (int64_t)std::min<size_t>((size_t)16 << 30, fr / 4);
+        budget = (int64_t)std::min<size_t>((size_t)64 << 30, fr / 3);
     }
     const uint64_t vhint = o && o->max_violations_hint > 0 ? (uint64_t)o->max_violations_hint : (1ull << 16);
 
@@ -350,6 +350,17 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
             J.nnz_stat = (uint64_t*)P8(off_state + sizeof(SlotState) * s + offsetof(SlotState, st_cpi));
             cpi_jobs.push_back(J);
         }
+    // per-chunk scratch of the compaction and index scans
+    const uint32_t cmp_chunks = compact_chunks(dg);
+    const size_t off_cmp_sums = L.take(4ull * cmp_chunks * std::max<size_t>(1, compact_jobs.size()));
+    for (size_t j = 0; j < compact_jobs.size(); j++)
+        compact_jobs[j].csum = (uint32_t*)P8(off_cmp_sums + 4ull * cmp_chunks * j);
+    uint64_t max_pcand = 0;
+    for (int s = 0; s < n; s++)
+        for (int i = 1; i < plans[s].k; i++) max_pcand = std::max<uint64_t>(max_pcand, descs[s].cand_cap[plans[s].lv[i].par]);
+    const uint32_t cpi_nch = cpi_chunks(max_pcand);
+    const size_t off_cpi_sums = L.take(8ull * cpi_nch * std::max<size_t>(1, cpi_jobs.size()));
+    for (size_t j = 0; j < cpi_jobs.size(); j++) cpi_jobs[j].csum = (uint64_t*)P8(off_cpi_sums + 8ull * cpi_nch * j);
     const size_t off_and = L.take(sizeof(AndJob) * std::max<size_t>(1, and_jobs.size()));
     const size_t off_cmp = L.take(sizeof(CompactJob) * std::max<size_t>(1, compact_jobs.size()));
     const size_t off_sct = L.take(sizeof(ScatterJob) * std::max<size_t>(1, scatter_jobs.size()));
@@ -423,6 +434,7 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
         J.rank = rb(J.rank);
         J.cand = rb(J.cand);
         J.count = rb(J.count);
+        J.csum = rb(J.csum);
     }
     for (auto& J : scatter_jobs) {
         J.qcand = rb(J.qcand);
@@ -444,6 +456,7 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
         J.off = rb(J.off);
         J.idx = rb(J.idx);
         J.nnz_stat = rb(J.nnz_stat);
+        J.csum = rb(J.csum);
     }
     // host image of [off_keys, L.size): keys, tmp (untouched), descs, zeroed
     // state/sched/tiles/err, job tables — uploaded in one copy
@@ -488,13 +501,14 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
             }
         }
         if (rc) return rc;
-        launches[PROF_REFINE] += ph.kind == 4 ? 0 : 1;
+        launches[PROF_REFINE] += ph.kind == 4 ? 0 : (ph.kind == 1 ? 2 : 1);
     }
     prof.end(PROF_REFINE, st);
     prof.begin(PROF_INDEX, st);
-    if (int rc = launch_cpi(dg, (const CpiJob*)(base + off_cpi), (int)cpi_jobs.size(), (int32_t*)(base + off_err), st))
+    if (int rc = launch_cpi(dg, (const CpiJob*)(base + off_cpi), (int)cpi_jobs.size(), cpi_nch,
+                            (int32_t*)(base + off_err), st))
         return rc;
-    launches[PROF_INDEX] += cpi_jobs.empty() ? 0 : 3;
+    launches[PROF_INDEX] += cpi_jobs.empty() ? 0 : 4;
     prof.end(PROF_INDEX, st);
 
     EnumArgs A;
