@@ -223,6 +223,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flags", type=int, default=0)
+    ap.add_argument("--budget-gb", type=float, default=0.0,
+                    help="frontier budget in GiB (0: the library default)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -256,8 +258,11 @@ def main():
     hint = 1 << 20
     l2_flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
+    budget = int(args.budget_gb * (1 << 30))
+
     def step():
-        return dg.validate_batch(qs, stream=stream, flags=flags, max_violations_hint=hint)
+        return dg.validate_batch(qs, stream=stream, flags=flags, max_violations_hint=hint,
+                                 frontier_budget_bytes=budget)
 
     for _ in range(args.warmup):
         res = step()

@@ -11,8 +11,9 @@
 //            the spanning-tree edge (parent(i), i): off u32 [|C(parent)|+1],
 //            idx i32 [nnz] = positions in C(i).
 //   frontier: per (GFD, level l >= 1) a buffer of partial matches, row-major
-//            [chunk][2(l+1)] i32 = l+1 vertex ids then l+1 candidate positions,
-//            plus the exclusive prefix of each row's fan-out u64 [chunk].
+//            [chunk][2(l+1)+1] i32 = l+1 vertex ids, l+1 candidate positions and
+//            the generator chosen for level l+1, plus the exclusive prefix of
+//            each row's fan-out u64 [chunk].
 #pragma once
 
 #include <cstdint>
@@ -63,6 +64,9 @@ struct LevelPlan {
     int8_t par;        // level of its spanning-tree parent (-1 at level 0)
     int8_t tdir;       // 1: tree edge parent -> u, 0: u -> parent
     int8_t nchk;       // number of entries in chk_q
+    int8_t ngen;       // number of alternative candidate generators in gen
+    int8_t gen[3];     // chk entries (required, not the tree parent) whose other
+                       // end's adjacency may generate the candidates instead
     int32_t tlab;      // tree edge label or GFD_WILDCARD
     uint32_t inj;      // bit q: v must differ from the vertex at level q
     int8_t chk_q[2 * MAXK];   // earlier level of each pair check

@@ -106,6 +106,30 @@ __device__ __forceinline__ uint32_t find_row(const uint64_t* S, uint64_t n, uint
     return (uint32_t)lo;
 }
 
+// r in [lo, hi) with S[r] <= w < S[r+1]: the search limited to the rows of a tile.
+__device__ __forceinline__ uint32_t find_row_in(const uint32_t* S, uint32_t lo, uint32_t hi, uint64_t w) {
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((uint64_t)__ldg(S + mid) <= w) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ uint32_t find_row_in(const uint64_t* S, uint32_t lo, uint32_t hi, uint64_t w) {
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldcg((const unsigned long long*)S + mid) <= w) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// position of v in the sorted candidate list of a level: O(1) from the bitmap
+// and its per-word popcount prefix
+__device__ __forceinline__ int32_t cand_rank(const uint32_t* bm, const uint32_t* rank, uint32_t v) {
+    return (int32_t)(__ldg(rank + (v >> 5)) + __popc(__ldg(bm + (v >> 5)) & ((1u << (v & 31)) - 1u)));
+}
+
 template <int NT>
 __device__ void expand_tiles(const EnumArgs& A) {
     using Scan = cub::BlockScan<uint64_t, NT>;
@@ -116,6 +140,7 @@ __device__ void expand_tiles(const EnumArgs& A) {
     } tmp;
     __shared__ uint64_t sh_base;
     __shared__ int32_t sh_slot;
+    __shared__ uint32_t sh_rlo, sh_rhi;
     const DevGraph& g = A.g;
     const uint32_t total_tiles = *(volatile uint32_t*)&A.sched->total_tiles;
     uint64_t probes = 0;
@@ -149,7 +174,19 @@ __device__ void expand_tiles(const EnumArgs& A) {
         const int32_t* rows_l = l >= 1 ? D->rows[l] : nullptr;
         const uint64_t nrows = k == 1 ? 0 : (l == 0 ? (uint64_t)S->ncand[0]
                                                     : (uint64_t)__ldcg((const unsigned long long*)&S->nrows[l]));
-        const int rw = 2 * (l + 1);  // row width at level l
+        const int rw = 2 * (l + 1) + 1;  // row width at level l: ids, positions, generator choice
+        if (threadIdx.x == 0 && k > 1) {
+            // the rows this tile's work items belong to
+            if (l == 0) {
+                sh_rlo = find_row(S0, nrows, wb);
+                sh_rhi = find_row(S0, nrows, we - 1);
+            } else {
+                sh_rlo = find_row(Sl, nrows, wb);
+                sh_rhi = find_row(Sl, nrows, we - 1);
+            }
+        }
+        __syncthreads();
+        const uint32_t rlo = sh_rlo, rhi1 = sh_rhi + 1;
         for (uint64_t w0 = wb; w0 < we; w0 += NT) {
             const uint64_t w = w0 + threadIdx.x;
             bool ok = w < we;
@@ -165,29 +202,57 @@ __device__ void expand_tiles(const EnumArgs& A) {
                 } else {
                     uint64_t o;
                     uint32_t pp;
+                    int choice = 0;
                     if (l == 0) {
-                        r = find_row(S0, nrows, w);
-                        o = w - S0[r];
+                        r = find_row_in(S0, rlo, rhi1, w);
+                        o = w - __ldg(S0 + r);
                         pp = r;
                         m[0] = (uint32_t)D->cand[0][r];
                     } else {
-                        r = find_row(Sl, nrows, w);
+                        r = find_row_in(Sl, rlo, rhi1, w);
                         o = w - __ldcg((const unsigned long long*)Sl + r);
                         rowp = rows_l + (uint64_t)r * rw;
                         for (int q = 0; q <= l; q++) m[q] = (uint32_t)__ldcg(rowp + q);
                         pp = (uint32_t)__ldcg(rowp + l + 1 + LP.par);
+                        choice = __ldcg(rowp + 2 * (l + 1));
                     }
-                    const uint32_t base = D->cpi_off[i][pp];
-                    j = D->cpi_idx[i][base + o];
-                    v = (uint32_t)D->cand[i][j];
+                    int skip = -1;
+                    if (choice == 0) {
+                        // candidates from the index edges of the spanning-tree parent
+                        const uint32_t base = __ldg(D->cpi_off[i] + pp);
+                        j = __ldg(D->cpi_idx[i] + base + o);
+                        v = (uint32_t)__ldg(D->cand[i] + j);
+                    } else {
+                        // candidates from the adjacency of the other end of a
+                        // required back edge (the shorter list): keep those in
+                        // C(u) and probe the spanning-tree edge instead
+                        const int cg = LP.gen[choice - 1];
+                        skip = cg;
+                        const uint32_t x = m[LP.chk_q[cg]];
+                        const uint32_t p = LP.chk_dir[cg] ? __ldg(g.in_adj + __ldg(g.in_off + x) + o)
+                                                          : __ldg(g.out_adj + __ldg(g.out_off + x) + o);
+                        v = p >> g.lbits;
+                        ok = exp_ok(LP.chk_exp[cg], (int32_t)(p & g.lmask)) &&
+                             ((__ldg(D->bm[i] + (v >> 5)) >> (v & 31)) & 1u);
+                        if (ok) {
+                            j = cand_rank(D->bm[i], D->rank[i], v);
+                            const uint32_t xp = m[LP.par];
+                            const int32_t gl =
+                                LP.tdir ? edge_label(g, xp, g.out_off[xp], g.out_off[xp + 1], v, g.in_off[v], g.in_off[v + 1])
+                                        : edge_label(g, v, g.out_off[v], g.out_off[v + 1], xp, g.in_off[xp], g.in_off[xp + 1]);
+                            probes++;
+                            ok = exp_ok(LP.tlab, gl);
+                        }
+                    }
                     // injectivity
-                    for (int q = 0; q <= l; q++)
+                    for (int q = 0; q <= l && ok; q++)
                         if (((LP.inj >> q) & 1u) && m[q] == v) ok = false;
-                    // every other pattern pair, both directions
+                    // every other pattern pair, both directions (required edges first)
                     if (ok && LP.nchk > 0) {
                         const uint32_t vo0 = g.out_off[v], vo1 = g.out_off[v + 1];
                         const uint32_t vi0 = g.in_off[v], vi1 = g.in_off[v + 1];
                         for (int c = 0; c < LP.nchk && ok; c++) {
+                            if (c == skip) continue;
                             const uint32_t x = m[LP.chk_q[c]];
                             int32_t gl;
                             if (LP.chk_dir[c]) gl = edge_label(g, v, vo0, vo1, x, g.in_off[x], g.in_off[x + 1]);
@@ -229,13 +294,26 @@ __device__ void expand_tiles(const EnumArgs& A) {
                     }
                 }
             } else {
-                // partial match of level i: append with its fan-out for level i+1
+                // partial match of level i: append it with its fan-out for level
+                // i+1, taken from the shortest candidate generator
                 uint64_t fo = 0;
+                int gen = 0;
                 if (ok) {
-                    const int pn = D->lv[i + 1].par;
+                    const LevelPlan& L2 = D->lv[i + 1];
+                    const int pn = L2.par;
                     const uint32_t ppn = pn == i ? (uint32_t)j : (l == 0 ? r : (uint32_t)__ldcg(rowp + l + 1 + pn));
                     const uint32_t* co = D->cpi_off[i + 1];
-                    fo = co[ppn + 1] - co[ppn];
+                    fo = __ldg(co + ppn + 1) - __ldg(co + ppn);
+                    for (int q = 0; q < L2.ngen; q++) {
+                        const int cg = L2.gen[q];
+                        const uint32_t x = m[L2.chk_q[cg]];
+                        const uint32_t d = L2.chk_dir[cg] ? __ldg(g.in_off + x + 1) - __ldg(g.in_off + x)
+                                                          : __ldg(g.out_off + x + 1) - __ldg(g.out_off + x);
+                        if (d < fo) {
+                            fo = d;
+                            gen = q + 1;
+                        }
+                    }
                 }
                 const uint64_t packed = ok ? ((1ull << ROW_SHIFT) | fo) : 0ull;
                 uint64_t excl, total;
@@ -254,7 +332,7 @@ __device__ void expand_tiles(const EnumArgs& A) {
                 if (ok) {
                     const uint64_t row = (sh_base >> ROW_SHIFT) + (excl >> ROW_SHIFT);
                     if (row < D->chunk) {
-                        const int nw = 2 * (i + 1);
+                        const int nw = 2 * (i + 1) + 1;
                         int32_t* dst = D->rows[i] + row * nw;
                         for (int q = 0; q <= i; q++) dst[q] = (int32_t)m[q];
                         if (l == 0) {
@@ -263,6 +341,7 @@ __device__ void expand_tiles(const EnumArgs& A) {
                             for (int q = 0; q <= l; q++) dst[i + 1 + q] = __ldcg(rowp + l + 1 + q);
                         }
                         dst[i + 1 + i] = j;
+                        dst[2 * (i + 1)] = gen;
                         D->wpre[i][row] = (sh_base & WORK_MASK) + (excl & WORK_MASK);
                     }
                 }

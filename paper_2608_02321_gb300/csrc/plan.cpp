@@ -234,6 +234,11 @@ int make_plan(const gfd_gfd* phi, int32_t n_attrs, const unsigned long long* lab
             }
         }
         L.nchk = (int8_t)n;
+        // alternative generators: required edges to earlier levels other than the
+        // spanning-tree parent (the adjacency of their image bounds the candidates)
+        L.ngen = 0;
+        for (int c = 0; c < n && L.ngen < 3; c++)
+            if (L.chk_exp[c] != EXP_NONE && L.chk_q[c] != L.par) L.gen[L.ngen++] = (int8_t)c;
         // candidate filter key (degrees without self-loops)
         FilterKey& K = P->key[i];
         K.label = phi->node_label[u];

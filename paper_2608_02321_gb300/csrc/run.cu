@@ -182,7 +182,7 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
         }
         for (size_t q = 0; q < P.lits.size(); q++) D.lit[q] = P.lits[q];
         uint64_t row_bytes = 0;
-        for (int l = 1; l <= P.k - 2; l++) row_bytes += 4ull * 2 * (l + 1) + 8;
+        for (int l = 1; l <= P.k - 2; l++) row_bytes += 4ull * (2 * (l + 1) + 1) + 8;
         uint64_t chunk = o && o->chunk_rows > 0 ? (uint64_t)o->chunk_rows
                                                 : (row_bytes ? (uint64_t)budget / n / row_bytes : (1ull << 24) - 1);
         chunk = std::max<uint64_t>(1024, std::min<uint64_t>(chunk, (1ull << 24) - 1));
@@ -203,7 +203,7 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
             F.cpi_idx[i] = L.take(4ull * std::max<uint64_t>(1, D.cpi_cap[i]));
         }
         for (int l = 1; l <= P.k - 2; l++) {
-            F.rows[l] = L.take(4ull * 2 * (l + 1) * chunk);
+            F.rows[l] = L.take(4ull * (2 * (l + 1) + 1) * chunk);
             F.wpre[l] = L.take(8ull * chunk);
         }
     }
