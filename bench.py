@@ -255,7 +255,7 @@ def main():
     stream = torch.cuda.current_stream()
     dg = G.Graph(g, stream=stream)
     flags = G.FLAG_PROFILE | args.flags
-    hint = 1 << 20
+    hint = 1 << 26   # violation records stored per call (all GFDs together)
     l2_flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
     budget = int(args.budget_gb * (1 << 30))

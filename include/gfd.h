@@ -132,7 +132,9 @@ typedef struct {
     int64_t frontier_budget_bytes; /* device bytes for partial-match buffers */
     int32_t chunk_rows;            /* partial matches expanded per step and GFD */
     int32_t block_threads;         /* threads per block of the expansion kernel */
-    int64_t max_violations_hint;   /* initial violation capacity per GFD */
+    int64_t max_violations_hint;   /* violations the run stores before it must
+                                      run again with exactly enough room (all
+                                      GFDs of a call together) */
     void *cuda_stream;             /* cudaStream_t to issue work on */
     int32_t flags;                 /* GFD_FLAG_* */
 } gfd_opts;
@@ -180,7 +182,7 @@ double gfd_result_profile(const gfd_result *r, int32_t which, int64_t *launches)
 /* Statistics of the run: 0 supersteps, 1 work items expanded, 2 partial
  * matches written, 3 edge-lookup probes (whole run), 4 candidate-list entries
  * (sum over pattern nodes), 5 index entries, 6 number of extra runs made
- * because the violations outgrew max_violations_hint. */
+ * because the violations of the call outgrew max_violations_hint. */
 uint64_t gfd_result_stat(const gfd_result *r, int32_t which);
 /* Release a result. */
 void gfd_result_free(gfd_result *r);

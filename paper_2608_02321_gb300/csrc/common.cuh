@@ -102,9 +102,6 @@ struct SlotDesc {
     int32_t* rows[MAXK];      // level l >= 1
     uint64_t* wpre[MAXK];     // level l >= 1
     uint64_t chunk;           // max work items per step (= row capacity)
-    // output
-    int32_t* viol;
-    uint64_t viol_cap;
 };
 
 // Mutable per-slot state (device).
@@ -137,6 +134,14 @@ struct Sched {
     uint64_t probes;
     uint64_t t_start;         // globaltimer at the first step
     uint64_t run_limit_ns;    // limit of the whole enumeration
+    // violations of all slots: records [slot, h(x_0), ..., h(x_{k-1})] of
+    // vstride ints appended at varena_used; records past varena_cap are counted
+    // but not stored
+    int32_t* varena;
+    uint64_t varena_cap;
+    uint64_t varena_used;
+    int32_t vstride;
+    int32_t pad2;
 };
 
 // device error codes (Sched::err, SlotState::err)

@@ -108,6 +108,9 @@ struct EnumArgs {
     int32_t tile;         // work items per tile
 };
 int enum_init(const EnumArgs& a, cudaStream_t st);
+// Split the violation arena (records [slot, tuple...]) into per-slot lists.
+int launch_split(const SlotDesc* slots, const int32_t* arena, uint64_t n, int32_t stride, int32_t* const* lists,
+                 unsigned long long* cursor, cudaStream_t st);
 // Runs supersteps until every slot is finished. persistent: one cooperative
 // launch; else a host loop (optionally captured into CUDA graphs).
 int enum_run(const EnumArgs& a, bool persistent, bool use_graph, int block_threads, cudaStream_t st,

@@ -138,9 +138,10 @@ __device__ void expand_tiles(const EnumArgs& A) {
         typename Scan::TempStorage scan;
         typename Reduce::TempStorage reduce;
     } tmp;
-    __shared__ uint64_t sh_base;
+    __shared__ uint64_t sh_base2[2];  // double-buffered: no barrier needed after its readers
     __shared__ int32_t sh_slot;
     __shared__ uint32_t sh_rlo, sh_rhi;
+    uint32_t parity = 0;
     const DevGraph& g = A.g;
     const uint32_t total_tiles = *(volatile uint32_t*)&A.sched->total_tiles;
     uint64_t probes = 0;
@@ -188,6 +189,8 @@ __device__ void expand_tiles(const EnumArgs& A) {
         __syncthreads();
         const uint32_t rlo = sh_rlo, rhi1 = sh_rhi + 1;
         for (uint64_t w0 = wb; w0 < we; w0 += NT) {
+            uint64_t& sh_base = sh_base2[parity];
+            parity ^= 1u;
             const uint64_t w = w0 + threadIdx.x;
             bool ok = w < we;
             uint32_t m[MAXK];
@@ -281,16 +284,20 @@ __device__ void expand_tiles(const EnumArgs& A) {
                 Scan(tmp.scan).ExclusiveSum(packed, excl, total);
                 if (threadIdx.x == 0) {
                     if (total >> 32) atomicAdd((unsigned long long*)&S->n_matches, (unsigned long long)(total >> 32));
-                    sh_base = (total & 0xffffffffu)
-                                  ? atomicAdd((unsigned long long*)&S->n_viol, (unsigned long long)(total & 0xffffffffu))
-                                  : 0;
+                    const unsigned long long nv = total & 0xffffffffu;
+                    sh_base = 0;
+                    if (nv) {
+                        atomicAdd((unsigned long long*)&S->n_viol, nv);
+                        sh_base = atomicAdd((unsigned long long*)&A.sched->varena_used, nv);
+                    }
                 }
                 __syncthreads();
                 if (viol) {
                     const uint64_t idx = sh_base + (excl & 0xffffffffu);
-                    if (idx < D->viol_cap) {
-                        int32_t* out = D->viol + idx * k;
-                        for (int q = 0; q < k; q++) out[D->order[q]] = (int32_t)m[q];
+                    if (idx < A.sched->varena_cap) {
+                        int32_t* rec = A.sched->varena + idx * A.sched->vstride;
+                        rec[0] = s;
+                        for (int q = 0; q < k; q++) rec[1 + D->order[q]] = (int32_t)m[q];
                     }
                 }
             } else {
@@ -346,7 +353,6 @@ __device__ void expand_tiles(const EnumArgs& A) {
                     }
                 }
             }
-            __syncthreads();
         }
         __syncthreads();
     }
@@ -569,7 +575,28 @@ int host_loop(const EnumArgs& a, bool use_graph, cudaStream_t st, int64_t* launc
     return rc;
 }
 
+// one thread per violation record: append it to its GFD's list
+__global__ void k_split(const SlotDesc* slots, const int32_t* arena, uint64_t n, int32_t stride,
+                        int32_t* const* lists, unsigned long long* cursor) {
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
+        const int32_t* rec = arena + r * stride;
+        const int s = rec[0];
+        const int k = slots[s].k;
+        const uint64_t pos = atomicAdd(&cursor[s], 1ull);
+        int32_t* dst = lists[s] + pos * k;
+        for (int q = 0; q < k; q++) dst[q] = rec[1 + q];
+    }
+}
+
 }  // namespace
+
+int launch_split(const SlotDesc* slots, const int32_t* arena, uint64_t n, int32_t stride, int32_t* const* lists,
+                 unsigned long long* cursor, cudaStream_t st) {
+    const int grid = (int)std::min<uint64_t>((n + 255) / 256, 152 * 16);
+    k_split<<<std::max(grid, 1), 256, 0, st>>>(slots, arena, n, stride, lists, cursor);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GFD_OK : cuda_fail(e, "k_split");
+}
 
 int enum_init(const EnumArgs& a, cudaStream_t st) {
     k_control<<<1, CTRL_THREADS, 0, st>>>(a, 1);

@@ -153,7 +153,8 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
         GFD_CUDA(cudaMemGetInfo(&fr, &tot));
         budget = (int64_t)std::min<size_t>((size_t)64 << 30, fr / 3);
     }
-    const uint64_t vhint = o && o->max_violations_hint > 0 ? (uint64_t)o->max_violations_hint : (1ull << 16);
+    // violation arena: records shared by all GFDs of the run
+    const uint64_t vcap = o && o->max_violations_hint > 0 ? (uint64_t)o->max_violations_hint : (1ull << 22);
 
     std::vector<SlotDesc> descs(n);
     Layout L;
@@ -215,6 +216,12 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
     const size_t off_sched = L.take(sizeof(Sched));
     const size_t off_tiles = L.take(4ull * (n + 1));
     const size_t off_err = L.take(4);
+    int kmax = 1;
+    for (auto& P : plans) kmax = std::max(kmax, P.k);
+    const int vstride = kmax + 1;
+    const size_t off_varena = L.take(4ull * vstride * vcap);
+    const size_t off_vptr = L.take(sizeof(int32_t*) * n);
+    const size_t off_vcur = L.take(8ull * n);
 
     // ---------------------------------------------------------------- job tables
     std::vector<AndJob> and_jobs;
@@ -386,29 +393,6 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
             if (p) cudaFreeAsync(p, st);
         }
     } pool_free{base, st};
-    // violation buffers, owned by the results
-    std::vector<int32_t*> vbuf(n, nullptr);
-    struct VFree {
-        std::vector<int32_t*>* v;
-        cudaStream_t st;
-        bool keep = false;
-        ~VFree() {
-            if (!keep)
-                for (auto p : *v)
-                    if (p) cudaFreeAsync(p, st);
-        }
-    } vfree{&vbuf, st};
-    for (int s = 0; s < n; s++) {
-        const uint64_t cap = vhint;
-        ce = cudaMallocFromPoolAsync((void**)&vbuf[s], std::max<uint64_t>(1, cap * plans[s].k) * 4, pool, st);
-        if (ce != cudaSuccess) {
-            cudaGetLastError();
-            set_error(GFD_ERR_OUT_OF_MEMORY, "violation buffer: %s", cudaGetErrorString(ce));
-            return GFD_ERR_OUT_OF_MEMORY;
-        }
-        descs[s].viol = vbuf[s];
-        descs[s].viol_cap = cap;
-    }
     // rebase every pool-relative pointer
     auto rb = [&](auto* p) -> decltype(p) {
         return p ? (decltype(p))(base + ((uint8_t*)p - (uint8_t*)nullptr)) : p;
@@ -468,6 +452,9 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
     sched.tile = (uint32_t)block_threads * 8;
     sched.timeout_ns = env_u64("GFD_WAIT_LIMIT_MS", 10000) * 1000000ull;
     sched.run_limit_ns = env_u64("GFD_RUN_LIMIT_MS", 600000) * 1000000ull;
+    sched.varena = (int32_t*)(base + off_varena);
+    sched.varena_cap = vcap;
+    sched.vstride = vstride;
     memcpy(img.data() + (off_sched - img0), &sched, sizeof(sched));
     memcpy(img.data() + (off_and - img0), and_jobs.data(), sizeof(AndJob) * and_jobs.size());
     memcpy(img.data() + (off_cmp - img0), compact_jobs.data(), sizeof(CompactJob) * compact_jobs.size());
@@ -541,35 +528,49 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
         set_error(GFD_ERR_OVERFLOW, "index capacity exceeded");
         return GFD_ERR_OVERFLOW;
     }
-    std::vector<int> redo;
-    for (int s = 0; s < n; s++) {
+    for (int s = 0; s < n; s++)
         if (states[s].err) {
             set_error(GFD_ERR_OVERFLOW, "GFD %d: partial-match counter overflow (lower chunk_rows)", s);
             return GFD_ERR_OVERFLOW;
         }
-        if (states[s].n_viol > descs[s].viol_cap) redo.push_back(s);
-    }
-    // GFDs whose violations did not fit: run them again with the exact capacity
-    std::vector<gfd_result*> redo_res(n, nullptr);
-    for (int s : redo) {
+    if (hs.varena_used > vcap) {
+        // the violations did not fit: run again with room for exactly all of them
         gfd_opts o2 = o ? *o : gfd_opts{};
-        o2.max_violations_hint = (int64_t)states[s].n_viol;
+        o2.max_violations_hint = (int64_t)hs.varena_used;
         o2.cuda_stream = st;
-        const gfd_gfd* one[1] = {phis[s]};
-        if (int rc = run_batch(g, one, 1, &o2, &redo_res[s])) {
-            for (auto r : redo_res)
-                if (r) delete r;
-            return rc;
+        const int rc = run_batch(g, phis, n, &o2, out);
+        if (rc == GFD_OK)
+            for (int s = 0; s < n; s++) out[s]->stat[6] += 1;
+        return rc;
+    }
+    // split the arena into one violation list per GFD (order within a list is
+    // arbitrary; gfd_result_tuples sorts)
+    std::vector<int32_t*> vbuf(n, nullptr);
+    struct VFree {
+        std::vector<int32_t*>* v;
+        cudaStream_t st;
+        ~VFree() {
+            for (auto p : *v)
+                if (p) cudaFreeAsync(p, st);
         }
+    } vfree{&vbuf, st};
+    for (int s = 0; s < n; s++) {
+        if (!states[s].n_viol) continue;
+        ce = cudaMallocFromPoolAsync((void**)&vbuf[s], 4ull * states[s].n_viol * plans[s].k, pool, st);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            set_error(GFD_ERR_OUT_OF_MEMORY, "violation list: %s", cudaGetErrorString(ce));
+            return GFD_ERR_OUT_OF_MEMORY;
+        }
+    }
+    if (hs.varena_used) {
+        GFD_CUDA(cudaMemcpyAsync(base + off_vptr, vbuf.data(), sizeof(int32_t*) * n, cudaMemcpyHostToDevice, st));
+        GFD_CUDA(cudaMemsetAsync(base + off_vcur, 0, 8ull * n, st));
+        if (int rc = launch_split(A.slots, sched.varena, hs.varena_used, vstride, (int32_t* const*)(base + off_vptr),
+                                  (unsigned long long*)(base + off_vcur), st))
+            return rc;
     }
     for (int s = 0; s < n; s++) {
-        if (redo_res[s]) {
-            out[s] = redo_res[s];
-            out[s]->stat[6] += 1;
-            cudaFreeAsync(vbuf[s], st);
-            vbuf[s] = nullptr;
-            continue;
-        }
         gfd_result* r = new gfd_result();
         r->k = plans[s].k;
         r->n_matches = states[s].n_matches;
