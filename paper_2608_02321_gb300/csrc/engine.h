@@ -21,6 +21,18 @@ struct gfd_graph {
     gfd::DevGraph dg{};
     std::vector<void*> allocs;
     std::vector<unsigned long long> label_stats;  // [65536][count, out-degree sum, in-degree sum]
+    std::vector<double> moments;                  // [65536][16], see PlanStats
+    std::vector<double> moments_all;              // [16]
+    std::vector<double> elabel_frac;              // [256]
+    gfd::PlanStats plan_stats() const {
+        gfd::PlanStats p;
+        p.n_vertices = n;
+        p.n_edges = m;
+        p.moments = moments.data();
+        p.moments_all = moments_all.data();
+        p.elabel_frac = elabel_frac.data();
+        return p;
+    }
     cudaStream_t stream = nullptr;
     gfd::Engine* eng = nullptr;
     std::mutex mu;

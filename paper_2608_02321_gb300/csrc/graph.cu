@@ -326,12 +326,37 @@ int graph_load(const gfd_graph_desc* d, const gfd_opts* o, gfd_graph** out) {
         CK(cudaMemcpyAsync(g->label_stats.data(), dstats, sizeof(unsigned long long) * 65536 * 3,
                            cudaMemcpyDeviceToHost, st));
     }
+    std::vector<uint32_t> h_in_off((size_t)n + 1);
+    CK(cudaMemcpyAsync(h_in_off.data(), in_off, sizeof(uint32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (bad) {
         set_error(GFD_ERR_INVALID_ARG, "gfd_graph_load:%s", bad_text(bad).c_str());
         return fail(GFD_ERR_INVALID_ARG);
     }
 #undef CK
+    // degree moments per vertex label and edge-label frequencies for planning
+    g->moments.assign((size_t)65536 * 16, 0.0);
+    g->moments_all.assign(16, 0.0);
+    for (int32_t v = 0; v < n; v++) {
+        const double dout = (double)(d->out_off[v + 1] - d->out_off[v]);
+        const double din = (double)(h_in_off[v + 1] - h_in_off[v]);
+        double* M = &g->moments[16 * (size_t)(d->vlabel[v] & 0xffff)];
+        double pa = 1.0;
+        for (int a = 0; a < 4; a++) {
+            double pb = pa;
+            for (int b = 0; b < 4; b++) {
+                M[4 * a + b] += pb;
+                pb *= din;
+            }
+            pa *= dout;
+        }
+    }
+    for (size_t L = 0; L < 65536; L++)
+        if (g->label_stats[3 * L])
+            for (int c = 0; c < 16; c++) g->moments_all[c] += g->moments[16 * L + c];
+    g->elabel_frac.assign(256, 0.0);
+    for (int64_t e = 0; e < m; e++) g->elabel_frac[d->out_elabel[e] & 255] += 1.0;
+    for (auto& f : g->elabel_frac) f /= (double)std::max<int64_t>(1, m);
     DevGraph& dg = g->dg;
     dg.n = n;
     dg.n_attrs = d->n_attrs;

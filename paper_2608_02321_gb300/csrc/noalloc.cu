@@ -162,7 +162,7 @@ int node_candidates_noalloc(const gfd_graph* g, const gfd_gfd* phi, int32_t node
         return GFD_ERR_UNSUPPORTED;
     }
     HostPlan plan;  // host memory only
-    if (int rc = make_plan(phi, g->n_attrs, g->label_stats.data(), g->n, &plan)) return rc;
+    if (int rc = make_plan(phi, g->n_attrs, g->plan_stats(), &plan)) return rc;
     const FilterKey key = plan.key[plan.level_of[node]];
     unsigned long long* scratch = nullptr;
     if (int rc = scratch_ptr(&scratch)) return rc;

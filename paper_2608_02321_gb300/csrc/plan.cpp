@@ -5,9 +5,15 @@
 // skeleton of Q (the vertices left after repeatedly removing vertices of
 // degree <= 1). Non-core vertices of skeleton degree > 1 form the forest, the
 // rest are leaves. The matching order is the core in breadth-first order from
-// the root, then the forest, then the leaves. The root (the vertex v_q from
-// which the compact path index is built, Section III.B step 1a) is the core
-// vertex with the fewest label candidates per skeleton edge. The spanning
+// the root, then the forest, then the leaves. The order inside each of the
+// three groups is cost-based, the way CFL-Match orders its paths: starting
+// from the root (the vertex v_q from which the compact path index is built,
+// Section III.B step 1a), the next vertex is the neighbour of the placed set
+// whose addition gives the smallest expected number of partial matches, where
+// the expectation is taken under the configuration model of the graph's degree
+// distribution per label (an edge a -> b with probability d_out(a) d_in(b) / |E|);
+// every core vertex is tried as the root and the order with the smallest sum of
+// expected partial matches over all prefixes wins. The spanning
 // tree of the index (step 1d) links every later vertex to its earliest-ordered
 // skeleton neighbour; all other pattern pairs are checked after a tree match is
 // found, including pairs WITHOUT a pattern edge, since a match may not contain
@@ -15,7 +21,9 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <limits>
 
 namespace gfd {
 
@@ -25,8 +33,7 @@ int32_t exp_of(int32_t qlab) { return qlab == NOEDGE ? EXP_NONE : qlab; }
 
 }  // namespace
 
-int make_plan(const gfd_gfd* phi, int32_t n_attrs, const unsigned long long* label_stats,
-              int64_t n_vertices, HostPlan* P) {
+int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostPlan* P) {
     if (!phi) {
         set_error(GFD_ERR_INVALID_ARG, "NULL GFD");
         return GFD_ERR_INVALID_ARG;
@@ -126,45 +133,92 @@ int make_plan(const gfd_gfd* phi, int32_t n_attrs, const unsigned long long* lab
     }
     bool any_core = false;
     for (int a = 0; a < k; a++) any_core |= core[a];
-    // root: fewest label candidates per skeleton edge among core vertices
-    auto label_count = [&](int32_t L) -> double {
-        if (L == GFD_WILDCARD) return (double)n_vertices;
-        return (double)label_stats[3 * (size_t)L];
+    // ---- cost model: log of the expected number of maps of the subpattern on
+    // a node set (degrees counted inside the set only)
+    const double NEG = -std::numeric_limits<double>::infinity();
+    auto log_moment = [&](int32_t L, int a, int b) -> double {
+        a = std::min(a, 3);
+        b = std::min(b, 3);
+        double m = stats.moments ? (L == GFD_WILDCARD ? stats.moments_all[4 * a + b]
+                                                      : stats.moments[16 * (size_t)L + 4 * a + b])
+                                 : 1.0;
+        return m > 0 ? std::log(m) : NEG;
     };
-    int root = 0;
-    double best = 1e300;
-    for (int a = 0; a < k; a++) {
-        if (any_core && !core[a]) continue;
-        double s = label_count(phi->node_label[a]) / (double)std::max(1, deg[a]);
-        if (s < best) {
-            best = s;
-            root = a;
+    const double logE = std::log((double)std::max<int64_t>(1, stats.n_edges));
+    auto log_est = [&](const bool* in) -> double {
+        double sum = 0;
+        for (int a = 0; a < k; a++) {
+            if (!in[a]) continue;
+            int dout = 0, din = 0;
+            for (int b = 0; b < k; b++) {
+                if (b == a || !in[b]) continue;
+                if (q[a][b] != NOEDGE) {
+                    dout++;
+                    double p = q[a][b] == GFD_WILDCARD || !stats.elabel_frac ? 1.0 : stats.elabel_frac[q[a][b]];
+                    sum += (p > 0 ? std::log(p) : NEG) - logE;
+                }
+                if (q[b][a] != NOEDGE) din++;
+            }
+            sum += log_moment(phi->node_label[a], dout, din);
+        }
+        return sum;
+    };
+    // greedy order from `root`: core, then forest, then leaves; returns the
+    // sum of expected partial matches over the prefixes
+    auto greedy = [&](int root, int* ord, int* core_end, int* forest_end) -> double {
+        bool in[MAXK] = {false};
+        in[root] = true;
+        ord[0] = root;
+        int nord = 1;
+        double cost = 0;
+        for (int phase = 0; phase < 3; phase++) {
+            for (;;) {
+                int best = -1;
+                double best_le = 0;
+                for (int u = 0; u < k; u++) {
+                    if (in[u]) continue;
+                    const bool grp = phase == 0 ? core[u] : phase == 1 ? (!core[u] && deg[u] > 1) : true;
+                    if (!grp) continue;
+                    bool touches = false;
+                    for (int h = 0; h < nord; h++) touches |= adj[ord[h]][u];
+                    if (!touches) continue;
+                    in[u] = true;
+                    const double le = log_est(in);
+                    in[u] = false;
+                    if (best < 0 || le < best_le) {
+                        best = u;
+                        best_le = le;
+                    }
+                }
+                if (best < 0) break;
+                in[best] = true;
+                ord[nord++] = best;
+                cost += std::exp(std::min(best_le, 700.0));
+            }
+            if (phase == 0) *core_end = nord;
+            if (phase == 1) *forest_end = nord;
+        }
+        return nord == k ? cost : std::numeric_limits<double>::infinity();
+    };
+    int best_root = -1;
+    double best_cost = 0;
+    for (int r = 0; r < k; r++) {
+        if (any_core && !core[r]) continue;
+        int ord[MAXK], ce = 0, fe = 0;
+        const double c = greedy(r, ord, &ce, &fe);
+        if (best_root < 0 || c < best_cost) {
+            best_root = r;
+            best_cost = c;
         }
     }
-    // order: core BFS, then forest BFS, then leaves
-    int pos[MAXK];
-    for (int a = 0; a < k; a++) pos[a] = -1;
-    int nord = 0;
-    auto bfs = [&](auto allowed) {
-        for (int h = 0; h < nord; h++) {
-            int a = P->order[h];
-            for (int b = 0; b < k; b++)
-                if (adj[a][b] && pos[b] < 0 && allowed(b)) {
-                    pos[b] = nord;
-                    P->order[nord++] = b;
-                }
+    {
+        int ce = 0, fe = 0;
+        if (greedy(best_root, P->order, &ce, &fe) == std::numeric_limits<double>::infinity()) {
+            set_error(GFD_ERR_INVALID_ARG, "internal: order incomplete");
+            return GFD_ERR_INVALID_ARG;
         }
-    };
-    pos[root] = 0;
-    P->order[nord++] = root;
-    bfs([&](int b) { return core[b]; });
-    P->core_size = nord;
-    bfs([&](int b) { return !core[b] && deg[b] > 1; });
-    P->forest_end = nord;
-    bfs([&](int b) { return true; });
-    if (nord != k) {
-        set_error(GFD_ERR_INVALID_ARG, "internal: order incomplete");
-        return GFD_ERR_INVALID_ARG;
+        P->core_size = ce;
+        P->forest_end = fe;
     }
     P->k = k;
     for (int i = 0; i < k; i++) P->level_of[P->order[i]] = i;

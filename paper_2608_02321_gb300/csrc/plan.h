@@ -33,9 +33,19 @@ struct HostPlan {
     int nx = 0, ny = 0, y_false = 0;
 };
 
-// label_count(L): number of data vertices with label L (GFD_WILDCARD: all).
+// Graph statistics used to order the pattern: per vertex label L the moments
+// M_L(a, b) = sum over vertices v with label L of d_out(v)^a * d_in(v)^b for
+// a, b in 0..3 (moments[16 * L + 4 * a + b]; moments_all over all vertices) and
+// the fraction of edges carrying each edge label.
+struct PlanStats {
+    int64_t n_vertices = 0;
+    int64_t n_edges = 0;
+    const double* moments = nullptr;      // [65536][16]
+    const double* moments_all = nullptr;  // [16]
+    const double* elabel_frac = nullptr;  // [256]
+};
+
 // Returns GFD_OK or an error code (message set).
-int make_plan(const gfd_gfd* phi, int32_t n_attrs, const unsigned long long* label_stats,
-              int64_t n_vertices, HostPlan* out);
+int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostPlan* out);
 
 }  // namespace gfd

@@ -120,7 +120,7 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
     // ---------------------------------------------------------------- plans
     std::vector<HostPlan> plans(n);
     for (int s = 0; s < n; s++) {
-        int rc = make_plan(phis[s], g->n_attrs, g->label_stats.data(), g->n, &plans[s]);
+        int rc = make_plan(phis[s], g->n_attrs, g->plan_stats(), &plans[s]);
         if (rc) return rc;
     }
     // filter keys (deduplicated across all GFDs and levels)
@@ -211,17 +211,19 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
     const size_t off_keybm = L.take(4ull * nwords * std::max(1, nkeys));
     const size_t off_keys = L.take(sizeof(FilterKey) * std::max(1, nkeys));
     const size_t off_tmp = L.take(4ull * nwords * std::max<size_t>(1, td_need));
-    const size_t off_desc = L.take(sizeof(SlotDesc) * n);
-    const size_t off_state = L.take(sizeof(SlotState) * n);
-    const size_t off_sched = L.take(sizeof(Sched));
-    const size_t off_tiles = L.take(4ull * (n + 1));
-    const size_t off_err = L.take(4);
+    // the violation arena and its split tables lie before the region that is
+    // uploaded from the host image (they need no initial contents)
     int kmax = 1;
     for (auto& P : plans) kmax = std::max(kmax, P.k);
     const int vstride = kmax + 1;
     const size_t off_varena = L.take(4ull * vstride * vcap);
     const size_t off_vptr = L.take(sizeof(int32_t*) * n);
     const size_t off_vcur = L.take(8ull * n);
+    const size_t off_desc = L.take(sizeof(SlotDesc) * n);
+    const size_t off_state = L.take(sizeof(SlotState) * n);
+    const size_t off_sched = L.take(sizeof(Sched));
+    const size_t off_tiles = L.take(4ull * (n + 1));
+    const size_t off_err = L.take(4);
 
     // ---------------------------------------------------------------- job tables
     std::vector<AndJob> and_jobs;
