@@ -35,6 +35,7 @@ extern "C" {
 
 typedef struct gfd_graph gfd_graph;    /* opaque, device-resident, library-owned */
 typedef struct gfd_result gfd_result;  /* opaque, library-owned */
+typedef struct gfd_session gfd_session; /* opaque serving session */
 
 enum {
     GFD_OK = 0,
@@ -186,6 +187,33 @@ double gfd_result_profile(const gfd_result *r, int32_t which, int64_t *launches)
 uint64_t gfd_result_stat(const gfd_result *r, int32_t which);
 /* Release a result. */
 void gfd_result_free(gfd_result *r);
+
+/*
+ * Serving session with continuous batching (Section II's validation problem
+ * answered per request). Requests are single GFDs, queued by
+ * gfd_session_submit. Each gfd_session_step admits queued requests, in arrival
+ * order, into free slots while their device memory (index, partial-match
+ * buffers and a violation buffer of opts->max_violations_hint tuples, default
+ * 2^20) fits opts->frontier_budget_bytes; builds their indexes together; then
+ * runs one round of enumeration steps over ALL running requests at once, so
+ * requests admitted later overlap on the device with those already running.
+ * Requests that finish in that round are moved to the result queue, read with
+ * gfd_session_next_result in completion order. The graph stays resident and
+ * the session's slot tables are reused across requests.
+ */
+int gfd_session_create(const gfd_graph *g, int32_t max_slots, const gfd_opts *opts,
+                       gfd_session **out);
+/* Queue one GFD (copied); *request_id identifies its result. The GFD is
+ * checked here: an invalid one is rejected with the usual error codes. */
+int gfd_session_submit(gfd_session *s, const gfd_gfd *phi, int64_t *request_id);
+/* Admit, run one round of enumeration steps, collect finished requests.
+ * *n_running and *n_queued (may be NULL) report the occupancy afterwards. */
+int gfd_session_step(gfd_session *s, int32_t *n_running, int32_t *n_queued);
+/* Pop one finished request: *request_id = -1 and *out = NULL when none is
+ * ready. The caller owns *out (gfd_result_free). */
+int gfd_session_next_result(gfd_session *s, int64_t *request_id, gfd_result **out);
+/* Wait for the session's work, release it and any uncollected results. */
+void gfd_session_free(gfd_session *s);
 
 /* Candidate filter of pattern node `node` of phi (its label, its out- and
  * in-degree in Q as lower bounds on the data vertex's degrees without

@@ -84,6 +84,11 @@ _SIGS = {
     "gfd_result_profile": (C.c_double, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
     "gfd_result_stat": (C.c_uint64, [C.c_void_p, C.c_int32]),
     "gfd_result_free": (None, [C.c_void_p]),
+    "gfd_session_create": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(gfd_opts), C.POINTER(C.c_void_p)]),
+    "gfd_session_submit": (C.c_int, [C.c_void_p, C.POINTER(gfd_gfd), C.POINTER(C.c_int64)]),
+    "gfd_session_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "gfd_session_next_result": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_void_p)]),
+    "gfd_session_free": (None, [C.c_void_p]),
     "gfd_node_candidates_noalloc": (C.c_int, [C.c_void_p, C.POINTER(gfd_gfd), C.c_int32, C.c_void_p,
                                               C.c_int64, C.POINTER(C.c_int64), C.c_void_p]),
     "gfd_last_error": (C.c_char_p, []),
@@ -281,6 +286,48 @@ class Graph:
         outs = (C.c_void_p * max(1, len(bufs)))()
         _check(_lib.gfd_validate_batch(self._h, arr, len(bufs), C.byref(o), outs))
         return [Result(C.c_void_p(outs[i])) for i in range(len(bufs))]
+
+
+class Session:
+    """A serving session with continuous batching (gfd_session_*): submit GFDs
+    at any time; each step admits queued requests into free slots within the
+    memory budget and advances every running request together."""
+
+    def __init__(self, g: Graph, max_slots: int = 64, **opts):
+        self._g = g  # keeps the graph alive
+        o = make_opts(**opts)
+        h = C.c_void_p(None)
+        _check(_lib.gfd_session_create(g._h, int(max_slots), C.byref(o), C.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.gfd_session_free(self._h)
+            self._h = None
+
+    def submit(self, gfd) -> int:
+        b = _GfdBuf(gfd)
+        rid = C.c_int64(-1)
+        _check(_lib.gfd_session_submit(self._h, C.byref(b.s), C.byref(rid)))
+        return int(rid.value)
+
+    def step(self):
+        """(running, queued) after one admission + enumeration round."""
+        r = C.c_int32(0)
+        q = C.c_int32(0)
+        _check(_lib.gfd_session_step(self._h, C.byref(r), C.byref(q)))
+        return int(r.value), int(q.value)
+
+    def results(self):
+        """All finished requests since the last call: [(request_id, Result)]."""
+        out = []
+        while True:
+            rid = C.c_int64(-1)
+            h = C.c_void_p(None)
+            _check(_lib.gfd_session_next_result(self._h, C.byref(rid), C.byref(h)))
+            if rid.value < 0:
+                return out
+            out.append((int(rid.value), Result(h)))
 
 
 def node_candidates_noalloc(g: Graph, gfd, node: int, out_ptr: int, out_cap: int, stream=None) -> int:

@@ -97,6 +97,24 @@ void gfd_result_free(gfd_result* r) {
     delete r;
 }
 
+int gfd_session_create(const gfd_graph* g, int32_t max_slots, const gfd_opts* opts, gfd_session** out) {
+    return gfd::session_create(const_cast<gfd_graph*>(g), max_slots, opts, out);
+}
+
+int gfd_session_submit(gfd_session* s, const gfd_gfd* phi, int64_t* request_id) {
+    return gfd::session_submit(s, phi, request_id);
+}
+
+int gfd_session_step(gfd_session* s, int32_t* n_running, int32_t* n_queued) {
+    return gfd::session_step(s, n_running, n_queued);
+}
+
+int gfd_session_next_result(gfd_session* s, int64_t* request_id, gfd_result** out) {
+    return gfd::session_next_result(s, request_id, out);
+}
+
+void gfd_session_free(gfd_session* s) { gfd::session_free(s); }
+
 const char* gfd_last_error(void) { return gfd::last_error_cstr(); }
 
 }  // extern "C"

@@ -102,6 +102,9 @@ struct SlotDesc {
     int32_t* rows[MAXK];      // level l >= 1
     uint64_t* wpre[MAXK];     // level l >= 1
     uint64_t chunk;           // max work items per step (= row capacity)
+    // violation output of this slot (serving); null: the run's shared arena
+    int32_t* viol;
+    uint64_t viol_cap;
 };
 
 // Mutable per-slot state (device).

@@ -120,6 +120,12 @@ struct EnumArgs {
     int32_t tile;         // work items per tile
 };
 int enum_init(const EnumArgs& a, cudaStream_t st);
+// Mark slots [0, n) idle; start the listed slots (host ids) after their index is built.
+int mark_idle(SlotState* state, int n, cudaStream_t st);
+int init_slots(const EnumArgs& a, const int* host_ids, int n, cudaStream_t st);
+// Capture `steps` enumeration steps (expand + control) into a CUDA graph.
+int capture_steps(const EnumArgs& a, int block_threads, int steps, cudaStream_t st, cudaGraph_t* graph,
+                  cudaGraphExec_t* exec);
 // Split the violation arena (records [slot, tuple...]) into per-slot lists.
 int launch_split(const SlotDesc* slots, const int32_t* arena, uint64_t n, int32_t stride, int32_t* const* lists,
                  unsigned long long* cursor, cudaStream_t st);
@@ -133,6 +139,11 @@ int graph_load(const gfd_graph_desc* d, const gfd_opts* o, gfd_graph** out);
 void graph_free(gfd_graph* g);
 void engine_free(Engine* e);
 int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opts* o, gfd_result** out);
+int session_create(gfd_graph* g, int32_t max_slots, const gfd_opts* o, gfd_session** out);
+void session_free(gfd_session* s);
+int session_submit(gfd_session* s, const gfd_gfd* phi, int64_t* id);
+int session_step(gfd_session* s, int32_t* n_running, int32_t* n_queued);
+int session_next_result(gfd_session* s, int64_t* id, gfd_result** out);
 int result_fetch(gfd_result* r);
 
 }  // namespace gfd

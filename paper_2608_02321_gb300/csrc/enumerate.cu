@@ -287,14 +287,21 @@ __device__ void expand_tiles(const EnumArgs& A) {
                     const unsigned long long nv = total & 0xffffffffu;
                     sh_base = 0;
                     if (nv) {
-                        atomicAdd((unsigned long long*)&S->n_viol, nv);
-                        sh_base = atomicAdd((unsigned long long*)&A.sched->varena_used, nv);
+                        const unsigned long long old = atomicAdd((unsigned long long*)&S->n_viol, nv);
+                        sh_base = D->viol ? old : atomicAdd((unsigned long long*)&A.sched->varena_used, nv);
                     }
                 }
                 __syncthreads();
                 if (viol) {
                     const uint64_t idx = sh_base + (excl & 0xffffffffu);
-                    if (idx < A.sched->varena_cap) {
+                    if (D->viol) {
+                        // the slot's own buffer: tuples in pattern-node order
+                        if (idx < D->viol_cap) {
+                            int32_t* out = D->viol + idx * k;
+                            for (int q = 0; q < k; q++) out[D->order[q]] = (int32_t)m[q];
+                        }
+                    } else if (idx < A.sched->varena_cap) {
+                        // the run's arena: [slot, tuple in pattern-node order]
                         int32_t* rec = A.sched->varena + idx * A.sched->vstride;
                         rec[0] = s;
                         for (int q = 0; q < k; q++) rec[1 + D->order[q]] = (int32_t)m[q];
@@ -361,6 +368,16 @@ __device__ void expand_tiles(const EnumArgs& A) {
     if (threadIdx.x == 0 && p) atomicAdd((unsigned long long*)&A.sched->probes, (unsigned long long)p);
 }
 
+// Start the enumeration of a slot whose index is built: level 0 holds the root
+// candidates, whose work items are the index edges to level 1.
+__device__ void slot_start(const SlotDesc* D, SlotState* S) {
+    S->cur = 0;
+    S->cursor[0] = 0;
+    S->cb = S->ce = 0;
+    S->nrows[0] = S->ncand[0];
+    S->total[0] = D->k == 1 ? (uint64_t)S->ncand[0] : (uint64_t)D->cpi_off[1][S->ncand[0]];
+}
+
 // One block: finish the last step of every slot and plan the next one.
 template <int CT>
 __device__ void control_step(const EnumArgs& A, bool first) {
@@ -387,10 +404,7 @@ __device__ void control_step(const EnumArgs& A, bool first) {
             SlotState* S = A.state + s;
             const int k = D->k;
             if (first) {
-                S->cur = 0;
-                S->cursor[0] = 0;
-                S->nrows[0] = S->ncand[0];
-                S->total[0] = k == 1 ? (uint64_t)S->ncand[0] : (uint64_t)D->cpi_off[1][S->ncand[0]];
+                slot_start(D, S);
             } else if (S->cur >= 0) {
                 const int l = S->cur;
                 S->cursor[l] = S->ce;
@@ -588,7 +602,45 @@ __global__ void k_split(const SlotDesc* slots, const int32_t* arena, uint64_t n,
     }
 }
 
+__global__ void k_mark_idle(SlotState* state, int n) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) state[s].cur = -1;
+}
+
+// Slots admitted between steps: start them (the next control step plans their
+// first chunk), finishing at once when level 0 has no work. The slot ids
+// travel in the kernel parameters.
+struct SlotIds {
+    int n;
+    int v[64];
+};
+
+__global__ void k_init_slots(EnumArgs A, SlotIds ids) {
+    const int i = threadIdx.x;
+    if (i >= ids.n) return;
+    const int s = ids.v[i];
+    SlotState* S = A.state + s;
+    slot_start(A.slots + s, S);
+    if (S->total[0] == 0) S->cur = -1;
+}
+
 }  // namespace
+
+int mark_idle(SlotState* state, int n, cudaStream_t st) {
+    k_mark_idle<<<std::max(1, (n + 255) / 256), 256, 0, st>>>(state, n);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GFD_OK : cuda_fail(e, "k_mark_idle");
+}
+
+int init_slots(const EnumArgs& a, const int* host_ids, int n, cudaStream_t st) {
+    for (int b = 0; b < n; b += 64) {
+        SlotIds ids{};
+        ids.n = std::min(64, n - b);
+        for (int i = 0; i < ids.n; i++) ids.v[i] = host_ids[b + i];
+        k_init_slots<<<1, 64, 0, st>>>(a, ids);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GFD_OK : cuda_fail(e, "k_init_slots");
+}
 
 int launch_split(const SlotDesc* slots, const int32_t* arena, uint64_t n, int32_t stride, int32_t* const* lists,
                  unsigned long long* cursor, cudaStream_t st) {
@@ -596,6 +648,23 @@ int launch_split(const SlotDesc* slots, const int32_t* arena, uint64_t n, int32_
     k_split<<<std::max(grid, 1), 256, 0, st>>>(slots, arena, n, stride, lists, cursor);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GFD_OK : cuda_fail(e, "k_split");
+}
+
+int capture_steps(const EnumArgs& a, int block_threads, int steps, cudaStream_t st, cudaGraph_t* graph,
+                  cudaGraphExec_t* exec) {
+    const int grid = block_threads == 512 ? expand_grid<512>() : expand_grid<256>();
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int it = 0; it < steps; it++) {
+            if (block_threads == 512) k_expand<512><<<grid, 512, 0, st>>>(a);
+            else k_expand<256><<<grid, 256, 0, st>>>(a);
+            k_control<<<1, CTRL_THREADS, 0, st>>>(a, 0);
+        }
+        e = cudaStreamEndCapture(st, graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, *graph, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "CUDA graph capture of the enumeration steps");
+    return GFD_OK;
 }
 
 int enum_init(const EnumArgs& a, cudaStream_t st) {

@@ -1,12 +1,20 @@
-// Orchestration of one validation run over a batch of GFD slots.
+// Orchestration of validation runs: batches (gfd_validate, gfd_validate_batch)
+// and continuous-batching serving sessions (gfd_session_*).
 //
-// Host: plan every GFD (plan.cpp), deduplicate candidate-filter keys across
-// GFDs (the shared candidate cache), derive every buffer's capacity from the
-// graph's per-label statistics, lay all device buffers out in one stream-
-// ordered allocation and upload all descriptors and job tables in one copy.
-// Device: one filter pass for all keys, the refinement and index phases (each
-// launch covers every GFD), then the enumeration driver. Nothing waits on the
-// host between phases; the host reads back the counters once at the end.
+// Device memory is organised in two kinds of blocks:
+//   - slot tables (one per run or session): a SlotDesc and a SlotState per GFD
+//     slot, the scheduler state, the per-step tile prefix and, for batch runs,
+//     the shared violation arena;
+//   - one workspace per group of GFDs admitted together: candidate bitmaps,
+//     ranks and lists, index edges, partial-match buffers, index-build job
+//     tables and scratch.
+// For a group the host plans every GFD (plan.cpp), deduplicates candidate-filter
+// keys across the group (the shared candidate cache), derives every buffer's
+// capacity from the graph's per-label statistics, allocates the workspace from
+// the graph's stream-ordered pool, uploads descriptors and job tables, and
+// launches one filter pass for all keys plus the refinement and index phases
+// (each launch covers every GFD of the group). Nothing waits on the host until
+// the counters are read back at the end.
 #include <cub/cub.cuh>
 
 #include <algorithm>
@@ -16,7 +24,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <map>
+#include <memory>
 #include <tuple>
 #include <vector>
 
@@ -39,7 +49,7 @@ namespace {
 constexpr int PROF_FILTER = 0, PROF_REFINE = 1, PROF_INDEX = 2, PROF_ENUM = 3;
 
 struct Layout {
-    size_t size = 256;  // offset 0 is reserved so that no buffer is at a null offset
+    size_t size = 256;  // offset 0 is reserved
     size_t take(size_t bytes) {
         size_t off = size;
         size = (size + bytes + 255) & ~(size_t)255;
@@ -61,6 +71,17 @@ int get_pool(gfd_graph* g, cudaMemPool_t* out) {
         GFD_CUDA(cudaMemPoolSetAttribute(g->eng->pool, cudaMemPoolAttrReleaseThreshold, &thr));
     }
     *out = g->eng->pool;
+    return GFD_OK;
+}
+
+int pool_alloc(cudaMemPool_t pool, size_t bytes, cudaStream_t st, void** out, const char* what) {
+    cudaError_t e = cudaMallocFromPoolAsync(out, std::max<size_t>(bytes, 256), pool, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        set_error(GFD_ERR_OUT_OF_MEMORY, "%s: %zu device bytes: %s", what, bytes, cudaGetErrorString(e));
+        return GFD_ERR_OUT_OF_MEMORY;
+    }
     return GFD_OK;
 }
 
@@ -102,76 +123,155 @@ struct ProfEvents {
 
 }  // namespace
 
-int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opts* o, gfd_result** out) {
-    if (!g || (!phis && n > 0) || !out || n < 0) {
-        set_error(GFD_ERR_INVALID_ARG, "validate: NULL argument");
-        return GFD_ERR_INVALID_ARG;
-    }
-    if (n == 0) return GFD_OK;
-    const DevGraph& dg = g->dg;
-    const uint32_t nwords = dg.nwords;
-    const int32_t flags = o ? o->flags : 0;
-    const bool refine = !(flags & GFD_FLAG_NO_REFINE);
-    const bool persistent = !(flags & GFD_FLAG_HOST_LOOP);
-    const bool use_graph = !(flags & GFD_FLAG_NO_GRAPH);
-    const int block_threads = (o && o->block_threads == 512) ? 512 : 256;
-    cudaStream_t st = (o && o->cuda_stream) ? (cudaStream_t)o->cuda_stream : g->stream;
+// ------------------------------------------------------------------ slot tables
+struct Tables {
+    int max_slots = 0;
+    uint8_t* base = nullptr;
+    SlotDesc* desc = nullptr;
+    SlotState* state = nullptr;
+    Sched* sched = nullptr;
+    uint32_t* tiles = nullptr;
+    int32_t* err = nullptr;
+    int32_t** vptr = nullptr;
+    unsigned long long* vcur = nullptr;
+    int32_t* varena = nullptr;  // batch runs only
+    uint64_t vcap = 0;
+    int vstride = 0;
+    int32_t tile = 2048;
+};
 
-    // ---------------------------------------------------------------- plans
-    std::vector<HostPlan> plans(n);
-    for (int s = 0; s < n; s++) {
-        int rc = make_plan(phis[s], g->n_attrs, g->plan_stats(), &plans[s]);
-        if (rc) return rc;
-    }
-    // filter keys (deduplicated across all GFDs and levels)
+namespace {
+
+int tables_alloc(cudaMemPool_t pool, int max_slots, int block_threads, int kmax_arena, uint64_t vcap,
+                 bool bounded_run, cudaStream_t st, Tables* T) {
+    Layout L;
+    const size_t o_desc = L.take(sizeof(SlotDesc) * max_slots);
+    const size_t o_state = L.take(sizeof(SlotState) * max_slots);
+    const size_t o_sched = L.take(sizeof(Sched));
+    const size_t o_tiles = L.take(4ull * (max_slots + 1));
+    const size_t o_err = L.take(4);
+    const size_t zero_end = L.size;
+    const size_t o_vptr = L.take(sizeof(int32_t*) * max_slots);
+    const size_t o_vcur = L.take(8ull * max_slots);
+    const int vstride = kmax_arena + 1;
+    const size_t o_arena = kmax_arena > 0 ? L.take(4ull * vstride * vcap) : 0;
+    void* base = nullptr;
+    if (int rc = pool_alloc(pool, L.size, st, &base, "slot tables")) return rc;
+    T->max_slots = max_slots;
+    T->base = (uint8_t*)base;
+    T->desc = (SlotDesc*)(T->base + o_desc);
+    T->state = (SlotState*)(T->base + o_state);
+    T->sched = (Sched*)(T->base + o_sched);
+    T->tiles = (uint32_t*)(T->base + o_tiles);
+    T->err = (int32_t*)(T->base + o_err);
+    T->vptr = (int32_t**)(T->base + o_vptr);
+    T->vcur = (unsigned long long*)(T->base + o_vcur);
+    T->varena = kmax_arena > 0 ? (int32_t*)(T->base + o_arena) : nullptr;
+    T->vcap = kmax_arena > 0 ? vcap : 0;
+    T->vstride = vstride;
+    T->tile = block_threads * 8;
+    GFD_CUDA(cudaMemsetAsync(T->base + o_desc, 0, zero_end - o_desc, st));
+    Sched s{};
+    s.n_slots = max_slots;
+    s.tile = (uint32_t)T->tile;
+    s.timeout_ns = env_u64("GFD_WAIT_LIMIT_MS", 10000) * 1000000ull;
+    // a run as a whole is bounded in time; a session's host drives bounded
+    // rounds of steps and has no overall limit
+    s.run_limit_ns = bounded_run ? env_u64("GFD_RUN_LIMIT_MS", 600000) * 1000000ull : UINT64_MAX;
+    s.varena = T->varena;
+    s.varena_cap = T->vcap;
+    s.vstride = vstride;
+    GFD_CUDA(cudaMemcpyAsync(T->sched, &s, sizeof(s), cudaMemcpyHostToDevice, st));
+    return GFD_OK;
+}
+
+EnumArgs enum_args(const gfd_graph* g, const Tables& T) {
+    EnumArgs A;
+    A.g = g->dg;
+    A.slots = T.desc;
+    A.state = T.state;
+    A.sched = T.sched;
+    A.tile_base = T.tiles;
+    A.n_slots = T.max_slots;
+    A.tile = T.tile;
+    return A;
+}
+
+// ------------------------------------------------------------------ groups
+struct Phase {
+    int kind;  // 0 and, 1 compact, 2 scatter, 3 prune, 4 clear marks
+    size_t first, count;
+};
+
+}  // namespace
+
+struct Group {
+    int n = 0;
+    std::vector<int> slot;
+    std::vector<HostPlan> plans;
+    std::vector<SlotDesc> descs;
+    std::vector<std::array<int, MAXK>> slot_key;
     std::vector<FilterKey> keys;
-    std::map<std::tuple<int32_t, uint32_t, uint32_t, int32_t>, int> key_id;
-    std::vector<std::array<int, MAXK>> slot_key(n);
+    uint8_t* base = nullptr;
+    size_t bytes = 0;
+    struct Off {
+        size_t bm[MAXK], rank[MAXK], cand[MAXK], cpi_off[MAXK], cpi_idx[MAXK], rows[MAXK], wpre[MAXK];
+    };
+    std::vector<Off> offs;
+    size_t o_keybm = 0, o_keys = 0, o_tmp = 0, o_cmp_sums = 0, o_cpi_sums = 0;
+    size_t o_jobs = 0, o_and = 0, o_cmp = 0, o_sct = 0, o_prn = 0, o_cpi = 0, jobs_end = 0;
+    uint32_t cmp_chunks = 1, cpi_nch = 1;
+    size_t td_need = 0;
+    std::vector<AndJob> and_jobs;
+    std::vector<CompactJob> compact_jobs;
+    std::vector<ScatterJob> scatter_jobs;
+    std::vector<PruneJob> prune_jobs;
+    std::vector<CpiJob> cpi_jobs;
+    std::vector<Phase> phases;
+    int live = 0;  // slots of this group still running (sessions)
+};
+
+namespace {
+
+// Plans, capacities and the workspace layout of a group (host only).
+int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* o, int64_t frontier_per_slot,
+               Group* G) {
+    const uint32_t nwords = g->dg.nwords;
+    G->n = n;
+    G->plans.resize(n);
     for (int s = 0; s < n; s++)
-        for (int i = 0; i < plans[s].k; i++) {
-            const FilterKey& K = plans[s].key[i];
+        if (int rc = make_plan(phis[s], g->n_attrs, g->plan_stats(), &G->plans[s])) return rc;
+    std::map<std::tuple<int32_t, uint32_t, uint32_t, int32_t>, int> key_id;
+    G->slot_key.resize(n);
+    for (int s = 0; s < n; s++)
+        for (int i = 0; i < G->plans[s].k; i++) {
+            const FilterKey& K = G->plans[s].key[i];
             auto t = std::make_tuple(K.label, K.dout_min, K.din_min, K.self_exp);
             auto it = key_id.find(t);
             if (it == key_id.end()) {
-                it = key_id.emplace(t, (int)keys.size()).first;
-                keys.push_back(K);
+                it = key_id.emplace(t, (int)G->keys.size()).first;
+                G->keys.push_back(K);
             }
-            slot_key[s][i] = it->second;
+            G->slot_key[s][i] = it->second;
         }
-    const int nkeys = (int)keys.size();
-
-    // ---------------------------------------------------------------- capacities
     auto lab_count = [&](int32_t L) -> uint64_t {
         return L == GFD_WILDCARD ? (uint64_t)g->n : (uint64_t)g->label_stats[3 * (size_t)L];
     };
     auto lab_deg = [&](int32_t L, bool outdir) -> uint64_t {
         return L == GFD_WILDCARD ? (uint64_t)g->m : (uint64_t)g->label_stats[3 * (size_t)L + (outdir ? 1 : 2)];
     };
-    int64_t budget = o && o->frontier_budget_bytes > 0 ? o->frontier_budget_bytes : 0;
-    if (!budget) {
-        size_t fr = 0, tot = 0;
-        GFD_CUDA(cudaMemGetInfo(&fr, &tot));
-        budget = (int64_t)std::min<size_t>((size_t)64 << 30, fr / 3);
-    }
-    // violation arena: records shared by all GFDs of the run
-    const uint64_t vcap = o && o->max_violations_hint > 0 ? (uint64_t)o->max_violations_hint : (1ull << 22);
-
-    std::vector<SlotDesc> descs(n);
     Layout L;
-    struct Off {
-        size_t bm[MAXK], rank[MAXK], cand[MAXK], cpi_off[MAXK], cpi_idx[MAXK], rows[MAXK], wpre[MAXK];
-    };
-    std::vector<Off> offs(n);
-    size_t td_need = 0;
+    G->descs.assign(n, SlotDesc{});
+    G->offs.resize(n);
     for (int lvl = 0; lvl < MAXK; lvl++) {
         size_t c = 0;
         for (int s = 0; s < n; s++)
-            if (lvl < plans[s].k) c += plans[s].td[lvl].size();
-        td_need = std::max(td_need, c);
+            if (lvl < G->plans[s].k) c += G->plans[s].td[lvl].size();
+        G->td_need = std::max(G->td_need, c);
     }
     for (int s = 0; s < n; s++) {
-        const HostPlan& P = plans[s];
-        SlotDesc& D = descs[s];
+        const HostPlan& P = G->plans[s];
+        SlotDesc& D = G->descs[s];
         memset(&D, 0, sizeof(D));
         D.k = P.k;
         D.nx = P.nx;
@@ -185,10 +285,10 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
         uint64_t row_bytes = 0;
         for (int l = 1; l <= P.k - 2; l++) row_bytes += 4ull * (2 * (l + 1) + 1) + 8;
         uint64_t chunk = o && o->chunk_rows > 0 ? (uint64_t)o->chunk_rows
-                                                : (row_bytes ? (uint64_t)budget / n / row_bytes : (1ull << 24) - 1);
+                                                : (row_bytes ? (uint64_t)frontier_per_slot / row_bytes : (1ull << 24) - 1);
         chunk = std::max<uint64_t>(1024, std::min<uint64_t>(chunk, (1ull << 24) - 1));
         D.chunk = chunk;
-        Off& F = offs[s];
+        Group::Off& F = G->offs[s];
         for (int i = 0; i < P.k; i++) {
             const int32_t lab = phis[s]->node_label[P.order[i]];
             D.cand_cap[i] = (uint32_t)std::min<uint64_t>(lab_count(lab), (uint64_t)g->n);
@@ -208,283 +308,216 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
             F.wpre[l] = L.take(8ull * chunk);
         }
     }
-    const size_t off_keybm = L.take(4ull * nwords * std::max(1, nkeys));
-    const size_t off_keys = L.take(sizeof(FilterKey) * std::max(1, nkeys));
-    const size_t off_tmp = L.take(4ull * nwords * std::max<size_t>(1, td_need));
-    // the violation arena and its split tables lie before the region that is
-    // uploaded from the host image (they need no initial contents)
-    int kmax = 1;
-    for (auto& P : plans) kmax = std::max(kmax, P.k);
-    const int vstride = kmax + 1;
-    const size_t off_varena = L.take(4ull * vstride * vcap);
-    const size_t off_vptr = L.take(sizeof(int32_t*) * n);
-    const size_t off_vcur = L.take(8ull * n);
-    const size_t off_desc = L.take(sizeof(SlotDesc) * n);
-    const size_t off_state = L.take(sizeof(SlotState) * n);
-    const size_t off_sched = L.take(sizeof(Sched));
-    const size_t off_tiles = L.take(4ull * (n + 1));
-    const size_t off_err = L.take(4);
-
-    // ---------------------------------------------------------------- job tables
-    std::vector<AndJob> and_jobs;
-    std::vector<CompactJob> compact_jobs;
-    std::vector<ScatterJob> scatter_jobs;
-    std::vector<PruneJob> prune_jobs;
-    std::vector<CpiJob> cpi_jobs;
-    struct Phase {
-        int kind;  // 0 and, 1 compact, 2 scatter, 3 prune, 4 memset tmp
-        size_t first, count;
-        int prof;
-    };
-    std::vector<Phase> phases;
-    // pointers are relative to the pool base until the pool exists: build with
-    // a null base, then add the base when uploading (see rebase below)
-    auto P8 = [](size_t off) { return (uint8_t*)nullptr + off; };
-    auto state_ncand = [&](int s, int i) {
-        return (uint32_t*)(P8(off_state + sizeof(SlotState) * s + offsetof(SlotState, ncand) + 4 * i));
-    };
-    auto keybm = [&](int key) { return (uint32_t*)P8(off_keybm + 4ull * nwords * key); };
-    int maxk = 0;
-    for (auto& P : plans) maxk = std::max(maxk, P.k);
+    const int nkeys = (int)G->keys.size();
+    G->o_keybm = L.take(4ull * nwords * std::max(1, nkeys));
+    G->o_tmp = L.take(4ull * nwords * std::max<size_t>(1, G->td_need));
+    // job counts, known before any pointer is
+    const bool refine = !(o && (o->flags & GFD_FLAG_NO_REFINE));
+    size_t n_compact = 0, n_cpi = 0, n_and = 0, n_sct = 0, n_prn = 0;
     for (int s = 0; s < n; s++) {
-        const HostPlan& P = plans[s];
-        SlotDesc& D = descs[s];
-        const Off& F = offs[s];
+        const HostPlan& P = G->plans[s];
+        n_cpi += P.k - 1;
+        n_and += P.k;
+        n_compact += P.k;
         for (int i = 0; i < P.k; i++) {
-            D.bm[i] = (uint32_t*)P8(F.bm[i]);
-            D.rank[i] = (uint32_t*)P8(F.rank[i]);
-            D.cand[i] = (int32_t*)P8(F.cand[i]);
+            n_sct += refine ? P.td[i].size() : 0;
+            const bool pr = refine && !P.bu[i].empty();
+            n_prn += pr;
+            n_compact += pr;
+        }
+    }
+    G->cmp_chunks = compact_chunks(g->dg);
+    uint64_t max_pcand = 0;
+    for (int s = 0; s < n; s++)
+        for (int i = 1; i < G->plans[s].k; i++)
+            max_pcand = std::max<uint64_t>(max_pcand, G->descs[s].cand_cap[G->plans[s].lv[i].par]);
+    G->cpi_nch = cpi_chunks(max_pcand);
+    G->o_cmp_sums = L.take(4ull * G->cmp_chunks * std::max<size_t>(1, n_compact));
+    G->o_cpi_sums = L.take(8ull * G->cpi_nch * std::max<size_t>(1, n_cpi));
+    // the region uploaded from the host: keys and job tables
+    G->o_jobs = L.size;
+    G->o_keys = L.take(sizeof(FilterKey) * std::max(1, nkeys));
+    G->o_and = L.take(sizeof(AndJob) * std::max<size_t>(1, n_and));
+    G->o_cmp = L.take(sizeof(CompactJob) * std::max<size_t>(1, n_compact));
+    G->o_sct = L.take(sizeof(ScatterJob) * std::max<size_t>(1, n_sct));
+    G->o_prn = L.take(sizeof(PruneJob) * std::max<size_t>(1, n_prn));
+    G->o_cpi = L.take(sizeof(CpiJob) * std::max<size_t>(1, n_cpi));
+    G->jobs_end = L.size;
+    G->bytes = L.size;
+    return GFD_OK;
+}
+
+// Absolute pointers, job tables and their upload; the descriptors go to the
+// slot tables at the group's slots, whose states are cleared.
+int group_build(gfd_graph* g, Group* G, const Tables& T, bool refine, cudaStream_t st) {
+    const uint32_t nwords = g->dg.nwords;
+    uint8_t* base = G->base;
+    const int n = G->n;
+    auto state_ncand = [&](int s, int i) { return &T.state[G->slot[s]].ncand[i]; };
+    auto keybm = [&](int key) { return (uint32_t*)(base + G->o_keybm + 4ull * nwords * key); };
+    int maxk = 0;
+    for (auto& P : G->plans) maxk = std::max(maxk, P.k);
+    for (int s = 0; s < n; s++) {
+        const HostPlan& P = G->plans[s];
+        SlotDesc& D = G->descs[s];
+        const Group::Off& F = G->offs[s];
+        for (int i = 0; i < P.k; i++) {
+            D.bm[i] = (uint32_t*)(base + F.bm[i]);
+            D.rank[i] = (uint32_t*)(base + F.rank[i]);
+            D.cand[i] = (int32_t*)(base + F.cand[i]);
             if (i >= 1) {
-                D.cpi_off[i] = (uint32_t*)P8(F.cpi_off[i]);
-                D.cpi_idx[i] = (int32_t*)P8(F.cpi_idx[i]);
+                D.cpi_off[i] = (uint32_t*)(base + F.cpi_off[i]);
+                D.cpi_idx[i] = (int32_t*)(base + F.cpi_idx[i]);
             }
         }
         for (int l = 1; l <= P.k - 2; l++) {
-            D.rows[l] = (int32_t*)P8(F.rows[l]);
-            D.wpre[l] = (uint64_t*)P8(F.wpre[l]);
+            D.rows[l] = (int32_t*)(base + F.rows[l]);
+            D.wpre[l] = (uint64_t*)(base + F.wpre[l]);
         }
     }
     auto compact_job = [&](int s, int i) {
-        CompactJob J;
-        J.bm = descs[s].bm[i];
-        J.rank = descs[s].rank[i];
-        J.cand = descs[s].cand[i];
+        CompactJob J{};
+        J.bm = G->descs[s].bm[i];
+        J.rank = G->descs[s].rank[i];
+        J.cand = G->descs[s].cand[i];
         J.count = state_ncand(s, i);
+        J.csum = (uint32_t*)(base + G->o_cmp_sums + 4ull * G->cmp_chunks * G->compact_jobs.size());
         return J;
     };
+    G->phases.clear();
     if (!refine) {
-        size_t a0 = and_jobs.size(), c0 = compact_jobs.size();
+        size_t a0 = G->and_jobs.size(), c0 = G->compact_jobs.size();
         for (int s = 0; s < n; s++)
-            for (int i = 0; i < plans[s].k; i++) {
+            for (int i = 0; i < G->plans[s].k; i++) {
                 AndJob J{};
-                J.bm = descs[s].bm[i];
-                J.src = keybm(slot_key[s][i]);
-                J.ntmp = 0;
-                and_jobs.push_back(J);
-                compact_jobs.push_back(compact_job(s, i));
+                J.bm = G->descs[s].bm[i];
+                J.src = keybm(G->slot_key[s][i]);
+                G->and_jobs.push_back(J);
+                G->compact_jobs.push_back(compact_job(s, i));
             }
-        phases.push_back({0, a0, and_jobs.size() - a0, PROF_REFINE});
-        phases.push_back({1, c0, compact_jobs.size() - c0, PROF_REFINE});
+        G->phases.push_back({0, a0, G->and_jobs.size() - a0});
+        G->phases.push_back({1, c0, G->compact_jobs.size() - c0});
     } else {
         // top-down, level by level
         for (int lvl = 0; lvl < maxk; lvl++) {
-            size_t a0 = and_jobs.size(), c0 = compact_jobs.size(), s0 = scatter_jobs.size();
+            size_t a0 = G->and_jobs.size(), c0 = G->compact_jobs.size(), s0 = G->scatter_jobs.size();
             size_t tmp_used = 0;
             for (int s = 0; s < n; s++) {
-                const HostPlan& P = plans[s];
+                const HostPlan& P = G->plans[s];
                 if (lvl >= P.k) continue;
                 AndJob J{};
-                J.bm = descs[s].bm[lvl];
-                J.src = keybm(slot_key[s][lvl]);
-                J.ntmp = 0;
+                J.bm = G->descs[s].bm[lvl];
+                J.src = keybm(G->slot_key[s][lvl]);
                 for (const Con& c : P.td[lvl]) {
-                    uint32_t* marks = (uint32_t*)P8(off_tmp + 4ull * nwords * tmp_used++);
+                    uint32_t* marks = (uint32_t*)(base + G->o_tmp + 4ull * nwords * tmp_used++);
                     ScatterJob S{};
-                    S.qcand = descs[s].cand[c.q];
+                    S.qcand = G->descs[s].cand[c.q];
                     S.qcount = state_ncand(s, c.q);
                     S.filter = J.src;
                     S.marks = marks;
                     // x needs an out-neighbour y in C(q) (x -> y): follow in-edges of y
                     S.scan_out = c.dir ? 0 : 1;
                     S.lab = c.lab;
-                    scatter_jobs.push_back(S);
+                    G->scatter_jobs.push_back(S);
                     J.tmp[J.ntmp++] = marks;
                 }
-                and_jobs.push_back(J);
-                compact_jobs.push_back(compact_job(s, lvl));
+                G->and_jobs.push_back(J);
+                G->compact_jobs.push_back(compact_job(s, lvl));
             }
-            if (tmp_used) phases.push_back({4, 0, tmp_used, PROF_REFINE});
-            if (scatter_jobs.size() > s0) phases.push_back({2, s0, scatter_jobs.size() - s0, PROF_REFINE});
-            phases.push_back({0, a0, and_jobs.size() - a0, PROF_REFINE});
-            phases.push_back({1, c0, compact_jobs.size() - c0, PROF_REFINE});
+            if (tmp_used) G->phases.push_back({4, 0, tmp_used});
+            if (G->scatter_jobs.size() > s0) G->phases.push_back({2, s0, G->scatter_jobs.size() - s0});
+            G->phases.push_back({0, a0, G->and_jobs.size() - a0});
+            G->phases.push_back({1, c0, G->compact_jobs.size() - c0});
         }
         // bottom-up, reverse level order
         for (int lvl = maxk - 1; lvl >= 0; lvl--) {
-            size_t p0 = prune_jobs.size(), c0 = compact_jobs.size();
+            size_t p0 = G->prune_jobs.size(), c0 = G->compact_jobs.size();
             for (int s = 0; s < n; s++) {
-                const HostPlan& P = plans[s];
+                const HostPlan& P = G->plans[s];
                 if (lvl >= P.k || P.bu[lvl].empty()) continue;
                 PruneJob J{};
-                J.cand = descs[s].cand[lvl];
+                J.cand = G->descs[s].cand[lvl];
                 J.count = state_ncand(s, lvl);
-                J.bm = descs[s].bm[lvl];
+                J.bm = G->descs[s].bm[lvl];
                 for (const Con& c : P.bu[lvl]) {
-                    J.con_bm[J.ncon] = descs[s].bm[c.q];
+                    J.con_bm[J.ncon] = G->descs[s].bm[c.q];
                     J.con_dir[J.ncon] = c.dir;
                     J.con_lab[J.ncon] = c.lab;
                     J.ncon++;
                 }
-                prune_jobs.push_back(J);
-                compact_jobs.push_back(compact_job(s, lvl));
+                G->prune_jobs.push_back(J);
+                G->compact_jobs.push_back(compact_job(s, lvl));
             }
-            if (prune_jobs.size() > p0) {
-                phases.push_back({3, p0, prune_jobs.size() - p0, PROF_REFINE});
-                phases.push_back({1, c0, compact_jobs.size() - c0, PROF_REFINE});
+            if (G->prune_jobs.size() > p0) {
+                G->phases.push_back({3, p0, G->prune_jobs.size() - p0});
+                G->phases.push_back({1, c0, G->compact_jobs.size() - c0});
             }
         }
     }
     for (int s = 0; s < n; s++)
-        for (int i = 1; i < plans[s].k; i++) {
-            const int par = plans[s].lv[i].par;
+        for (int i = 1; i < G->plans[s].k; i++) {
+            const int par = G->plans[s].lv[i].par;
             CpiJob J{};
-            J.pcand = descs[s].cand[par];
+            J.pcand = G->descs[s].cand[par];
             J.pcount = state_ncand(s, par);
-            J.cbm = descs[s].bm[i];
-            J.crank = descs[s].rank[i];
-            J.off = descs[s].cpi_off[i];
-            J.idx = descs[s].cpi_idx[i];
-            J.cap = descs[s].cpi_cap[i];
-            J.out = plans[s].lv[i].tdir;
-            J.lab = plans[s].lv[i].tlab;
-            J.nnz_stat = (uint64_t*)P8(off_state + sizeof(SlotState) * s + offsetof(SlotState, st_cpi));
-            cpi_jobs.push_back(J);
+            J.cbm = G->descs[s].bm[i];
+            J.crank = G->descs[s].rank[i];
+            J.off = G->descs[s].cpi_off[i];
+            J.idx = G->descs[s].cpi_idx[i];
+            J.cap = G->descs[s].cpi_cap[i];
+            J.out = G->plans[s].lv[i].tdir;
+            J.lab = G->plans[s].lv[i].tlab;
+            J.nnz_stat = &T.state[G->slot[s]].st_cpi;
+            J.csum = (uint64_t*)(base + G->o_cpi_sums + 8ull * G->cpi_nch * G->cpi_jobs.size());
+            G->cpi_jobs.push_back(J);
         }
-    // per-chunk scratch of the compaction and index scans
-    const uint32_t cmp_chunks = compact_chunks(dg);
-    const size_t off_cmp_sums = L.take(4ull * cmp_chunks * std::max<size_t>(1, compact_jobs.size()));
-    for (size_t j = 0; j < compact_jobs.size(); j++)
-        compact_jobs[j].csum = (uint32_t*)P8(off_cmp_sums + 4ull * cmp_chunks * j);
-    uint64_t max_pcand = 0;
-    for (int s = 0; s < n; s++)
-        for (int i = 1; i < plans[s].k; i++) max_pcand = std::max<uint64_t>(max_pcand, descs[s].cand_cap[plans[s].lv[i].par]);
-    const uint32_t cpi_nch = cpi_chunks(max_pcand);
-    const size_t off_cpi_sums = L.take(8ull * cpi_nch * std::max<size_t>(1, cpi_jobs.size()));
-    for (size_t j = 0; j < cpi_jobs.size(); j++) cpi_jobs[j].csum = (uint64_t*)P8(off_cpi_sums + 8ull * cpi_nch * j);
-    const size_t off_and = L.take(sizeof(AndJob) * std::max<size_t>(1, and_jobs.size()));
-    const size_t off_cmp = L.take(sizeof(CompactJob) * std::max<size_t>(1, compact_jobs.size()));
-    const size_t off_sct = L.take(sizeof(ScatterJob) * std::max<size_t>(1, scatter_jobs.size()));
-    const size_t off_prn = L.take(sizeof(PruneJob) * std::max<size_t>(1, prune_jobs.size()));
-    const size_t off_cpi = L.take(sizeof(CpiJob) * std::max<size_t>(1, cpi_jobs.size()));
-    const size_t upload_begin = off_keys;  // keys .. end are uploaded from one host image
-    (void)upload_begin;
-
-    // ---------------------------------------------------------------- allocate
-    cudaMemPool_t pool;
-    if (int rc = get_pool(g, &pool)) return rc;
-    uint8_t* base = nullptr;
-    cudaError_t ce = cudaMallocFromPoolAsync((void**)&base, L.size, pool, st);
-    if (ce != cudaSuccess) {
-        cudaGetLastError();
-        set_error(GFD_ERR_OUT_OF_MEMORY, "device workspace of %zu bytes: %s", L.size, cudaGetErrorString(ce));
-        return GFD_ERR_OUT_OF_MEMORY;
-    }
-    struct PoolFree {
-        uint8_t* p;
-        cudaStream_t st;
-        ~PoolFree() {
-            if (p) cudaFreeAsync(p, st);
-        }
-    } pool_free{base, st};
-    // rebase every pool-relative pointer
-    auto rb = [&](auto* p) -> decltype(p) {
-        return p ? (decltype(p))(base + ((uint8_t*)p - (uint8_t*)nullptr)) : p;
+    // one host image of keys and job tables
+    std::vector<uint8_t> img(G->jobs_end - G->o_jobs, 0);
+    auto put = [&](size_t off, const void* p, size_t bytes) {
+        if (bytes) memcpy(img.data() + (off - G->o_jobs), p, bytes);
     };
-    for (auto& D : descs) {
-        for (int i = 0; i < MAXK; i++) {
-            D.bm[i] = rb(D.bm[i]);
-            D.rank[i] = rb(D.rank[i]);
-            D.cand[i] = rb(D.cand[i]);
-            D.cpi_off[i] = rb(D.cpi_off[i]);
-            D.cpi_idx[i] = rb(D.cpi_idx[i]);
-            D.rows[i] = rb(D.rows[i]);
-            D.wpre[i] = rb(D.wpre[i]);
-        }
+    put(G->o_keys, G->keys.data(), sizeof(FilterKey) * G->keys.size());
+    put(G->o_and, G->and_jobs.data(), sizeof(AndJob) * G->and_jobs.size());
+    put(G->o_cmp, G->compact_jobs.data(), sizeof(CompactJob) * G->compact_jobs.size());
+    put(G->o_sct, G->scatter_jobs.data(), sizeof(ScatterJob) * G->scatter_jobs.size());
+    put(G->o_prn, G->prune_jobs.data(), sizeof(PruneJob) * G->prune_jobs.size());
+    put(G->o_cpi, G->cpi_jobs.data(), sizeof(CpiJob) * G->cpi_jobs.size());
+    GFD_CUDA(cudaMemcpyAsync(base + G->o_jobs, img.data(), img.size(), cudaMemcpyHostToDevice, st));
+    // descriptors into the slot tables (contiguous runs in one copy), states cleared
+    for (int s = 0; s < n;) {
+        int e = s + 1;
+        while (e < n && G->slot[e] == G->slot[e - 1] + 1) e++;
+        GFD_CUDA(cudaMemcpyAsync(&T.desc[G->slot[s]], &G->descs[s], sizeof(SlotDesc) * (e - s),
+                                 cudaMemcpyHostToDevice, st));
+        GFD_CUDA(cudaMemsetAsync(&T.state[G->slot[s]], 0, sizeof(SlotState) * (e - s), st));
+        s = e;
     }
-    for (auto& J : and_jobs) {
-        J.bm = rb(J.bm);
-        J.src = rb(J.src);
-        for (int t = 0; t < J.ntmp; t++) J.tmp[t] = rb(J.tmp[t]);
-    }
-    for (auto& J : compact_jobs) {
-        J.bm = rb(J.bm);
-        J.rank = rb(J.rank);
-        J.cand = rb(J.cand);
-        J.count = rb(J.count);
-        J.csum = rb(J.csum);
-    }
-    for (auto& J : scatter_jobs) {
-        J.qcand = rb(J.qcand);
-        J.qcount = rb(J.qcount);
-        J.filter = rb(J.filter);
-        J.marks = rb(J.marks);
-    }
-    for (auto& J : prune_jobs) {
-        J.cand = rb(J.cand);
-        J.count = rb(J.count);
-        J.bm = rb(J.bm);
-        for (int c = 0; c < J.ncon; c++) J.con_bm[c] = rb(J.con_bm[c]);
-    }
-    for (auto& J : cpi_jobs) {
-        J.pcand = rb(J.pcand);
-        J.pcount = rb(J.pcount);
-        J.cbm = rb(J.cbm);
-        J.crank = rb(J.crank);
-        J.off = rb(J.off);
-        J.idx = rb(J.idx);
-        J.nnz_stat = rb(J.nnz_stat);
-        J.csum = rb(J.csum);
-    }
-    // host image of [off_keys, L.size): keys, tmp (untouched), descs, zeroed
-    // state/sched/tiles/err, job tables — uploaded in one copy
-    const size_t img0 = off_desc;
-    std::vector<uint8_t> img(L.size - img0, 0);
-    memcpy(img.data() + (off_desc - img0), descs.data(), sizeof(SlotDesc) * n);
-    Sched sched{};
-    sched.n_slots = n;
-    sched.tile = (uint32_t)block_threads * 8;
-    sched.timeout_ns = env_u64("GFD_WAIT_LIMIT_MS", 10000) * 1000000ull;
-    sched.run_limit_ns = env_u64("GFD_RUN_LIMIT_MS", 600000) * 1000000ull;
-    sched.varena = (int32_t*)(base + off_varena);
-    sched.varena_cap = vcap;
-    sched.vstride = vstride;
-    memcpy(img.data() + (off_sched - img0), &sched, sizeof(sched));
-    memcpy(img.data() + (off_and - img0), and_jobs.data(), sizeof(AndJob) * and_jobs.size());
-    memcpy(img.data() + (off_cmp - img0), compact_jobs.data(), sizeof(CompactJob) * compact_jobs.size());
-    memcpy(img.data() + (off_sct - img0), scatter_jobs.data(), sizeof(ScatterJob) * scatter_jobs.size());
-    memcpy(img.data() + (off_prn - img0), prune_jobs.data(), sizeof(PruneJob) * prune_jobs.size());
-    memcpy(img.data() + (off_cpi - img0), cpi_jobs.data(), sizeof(CpiJob) * cpi_jobs.size());
-    ProfEvents prof;
-    if (int rc = prof.init((flags & GFD_FLAG_PROFILE) != 0)) return rc;
-    int64_t launches[5] = {0, 0, 0, 0, 0};
-    GFD_CUDA(cudaMemcpyAsync(base + off_keys, keys.data(), sizeof(FilterKey) * nkeys, cudaMemcpyHostToDevice, st));
-    GFD_CUDA(cudaMemcpyAsync(base + img0, img.data(), img.size(), cudaMemcpyHostToDevice, st));
+    return GFD_OK;
+}
 
-    // ---------------------------------------------------------------- device phases
+int group_launch(gfd_graph* g, Group* G, const Tables& T, cudaStream_t st, ProfEvents& prof, int64_t* launches) {
+    const DevGraph& dg = g->dg;
+    uint8_t* base = G->base;
     prof.begin(PROF_FILTER, st);
-    if (int rc = launch_filter(dg, (const FilterKey*)(base + off_keys), nkeys, (uint32_t*)(base + off_keybm), st))
+    if (int rc = launch_filter(dg, (const FilterKey*)(base + G->o_keys), (int)G->keys.size(),
+                               (uint32_t*)(base + G->o_keybm), st))
         return rc;
     launches[PROF_FILTER]++;
     prof.end(PROF_FILTER, st);
     prof.begin(PROF_REFINE, st);
-    for (const Phase& ph : phases) {
+    for (const Phase& ph : G->phases) {
         int rc = GFD_OK;
         switch (ph.kind) {
-            case 0: rc = launch_and(dg, (const AndJob*)(base + off_and) + ph.first, (int)ph.count, st); break;
-            case 1: rc = launch_compact(dg, (const CompactJob*)(base + off_cmp) + ph.first, (int)ph.count, st); break;
-            case 2: rc = launch_scatter(dg, (const ScatterJob*)(base + off_sct) + ph.first, (int)ph.count, st); break;
-            case 3: rc = launch_prune(dg, (const PruneJob*)(base + off_prn) + ph.first, (int)ph.count, st); break;
+            case 0: rc = launch_and(dg, (const AndJob*)(base + G->o_and) + ph.first, (int)ph.count, st); break;
+            case 1:
+                rc = launch_compact(dg, (const CompactJob*)(base + G->o_cmp) + ph.first, (int)ph.count, st);
+                break;
+            case 2:
+                rc = launch_scatter(dg, (const ScatterJob*)(base + G->o_sct) + ph.first, (int)ph.count, st);
+                break;
+            case 3: rc = launch_prune(dg, (const PruneJob*)(base + G->o_prn) + ph.first, (int)ph.count, st); break;
             case 4: {
-                cudaError_t e = cudaMemsetAsync(base + off_tmp, 0, 4ull * nwords * ph.count, st);
+                cudaError_t e = cudaMemsetAsync(base + G->o_tmp, 0, 4ull * dg.nwords * ph.count, st);
                 rc = e == cudaSuccess ? GFD_OK : cuda_fail(e, "cudaMemsetAsync");
                 break;
             }
@@ -494,33 +527,99 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
     }
     prof.end(PROF_REFINE, st);
     prof.begin(PROF_INDEX, st);
-    if (int rc = launch_cpi(dg, (const CpiJob*)(base + off_cpi), (int)cpi_jobs.size(), cpi_nch,
-                            (int32_t*)(base + off_err), st))
+    if (int rc = launch_cpi(dg, (const CpiJob*)(base + G->o_cpi), (int)G->cpi_jobs.size(), G->cpi_nch, T.err, st))
         return rc;
-    launches[PROF_INDEX] += cpi_jobs.empty() ? 0 : 4;
+    launches[PROF_INDEX] += G->cpi_jobs.empty() ? 0 : 4;
     prof.end(PROF_INDEX, st);
+    return GFD_OK;
+}
 
-    EnumArgs A;
-    A.g = dg;
-    A.slots = (const SlotDesc*)(base + off_desc);
-    A.state = (SlotState*)(base + off_state);
-    A.sched = (Sched*)(base + off_sched);
-    A.tile_base = (uint32_t*)(base + off_tiles);
-    A.n_slots = n;
-    A.tile = (int32_t)sched.tile;
+int64_t default_budget(const gfd_opts* o) {
+    if (o && o->frontier_budget_bytes > 0) return o->frontier_budget_bytes;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return (int64_t)1 << 32;
+    }
+    return (int64_t)std::min<size_t>((size_t)64 << 30, fr / 3);
+}
+
+gfd_result* make_result(const HostPlan& P, const SlotState& S, uint64_t steps, uint64_t probes, int32_t* d_viol,
+                        cudaStream_t st) {
+    gfd_result* r = new gfd_result();
+    r->k = P.k;
+    r->n_matches = S.n_matches;
+    r->n_viol = S.n_viol;
+    r->d_viol = d_viol;
+    r->stream = st;
+    r->stat[0] = steps;
+    r->stat[1] = S.st_work;
+    r->stat[2] = S.st_rows;
+    r->stat[3] = probes;
+    uint64_t nc = 0;
+    for (int i = 0; i < P.k; i++) nc += S.ncand[i];
+    r->stat[4] = nc;
+    r->stat[5] = S.st_cpi;
+    return r;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ batch runs
+int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opts* o, gfd_result** out) {
+    if (!g || (!phis && n > 0) || !out || n < 0) {
+        set_error(GFD_ERR_INVALID_ARG, "validate: NULL argument");
+        return GFD_ERR_INVALID_ARG;
+    }
+    if (n == 0) return GFD_OK;
+    const int32_t flags = o ? o->flags : 0;
+    const bool refine = !(flags & GFD_FLAG_NO_REFINE);
+    const bool persistent = !(flags & GFD_FLAG_HOST_LOOP);
+    const bool use_graph = !(flags & GFD_FLAG_NO_GRAPH);
+    const int block_threads = (o && o->block_threads == 512) ? 512 : 256;
+    cudaStream_t st = (o && o->cuda_stream) ? (cudaStream_t)o->cuda_stream : g->stream;
+    const uint64_t vcap = o && o->max_violations_hint > 0 ? (uint64_t)o->max_violations_hint : (1ull << 22);
+
+    Group G;
+    if (int rc = group_plan(g, phis, n, o, default_budget(o) / n, &G)) return rc;
+    int kmax = 1;
+    for (auto& P : G.plans) kmax = std::max(kmax, P.k);
+    cudaMemPool_t pool;
+    if (int rc = get_pool(g, &pool)) return rc;
+    Tables T;
+    if (int rc = tables_alloc(pool, n, block_threads, kmax, vcap, true, st, &T)) return rc;
+    struct Free {
+        std::vector<void*> p;
+        cudaStream_t st;
+        ~Free() {
+            for (void* q : p)
+                if (q) cudaFreeAsync(q, st);
+        }
+    } fr{{T.base}, st};
+    void* wb = nullptr;
+    if (int rc = pool_alloc(pool, G.bytes, st, &wb, "device workspace")) return rc;
+    fr.p.push_back(wb);
+    G.base = (uint8_t*)wb;
+    G.slot.resize(n);
+    for (int s = 0; s < n; s++) G.slot[s] = s;
+    if (int rc = group_build(g, &G, T, refine, st)) return rc;
+    ProfEvents prof;
+    if (int rc = prof.init((flags & GFD_FLAG_PROFILE) != 0)) return rc;
+    int64_t launches[5] = {0, 0, 0, 0, 0};
+    if (int rc = group_launch(g, &G, T, st, prof, launches)) return rc;
+    const EnumArgs A = enum_args(g, T);
     if (int rc = enum_init(A, st)) return rc;
     if (int rc = enum_run(A, persistent, use_graph, block_threads, st, prof.on ? prof.ev[2 * PROF_ENUM] : nullptr,
                           prof.on ? prof.ev[2 * PROF_ENUM + 1] : nullptr, &launches[PROF_ENUM]))
         return rc;
     launches[PROF_ENUM] += 1;
 
-    // ---------------------------------------------------------------- read back
     std::vector<SlotState> states(n);
     Sched hs{};
     int32_t herr = 0;
-    GFD_CUDA(cudaMemcpyAsync(states.data(), base + off_state, sizeof(SlotState) * n, cudaMemcpyDeviceToHost, st));
-    GFD_CUDA(cudaMemcpyAsync(&hs, base + off_sched, sizeof(Sched), cudaMemcpyDeviceToHost, st));
-    GFD_CUDA(cudaMemcpyAsync(&herr, base + off_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    GFD_CUDA(cudaMemcpyAsync(states.data(), T.state, sizeof(SlotState) * n, cudaMemcpyDeviceToHost, st));
+    GFD_CUDA(cudaMemcpyAsync(&hs, T.sched, sizeof(Sched), cudaMemcpyDeviceToHost, st));
+    GFD_CUDA(cudaMemcpyAsync(&herr, T.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     GFD_CUDA(cudaStreamSynchronize(st));
     if (hs.err == DERR_TIMEOUT) {
         set_error(GFD_ERR_TIMEOUT, "a device-side limit ran out (grid barrier wait or enumeration time)");
@@ -558,46 +657,294 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
     } vfree{&vbuf, st};
     for (int s = 0; s < n; s++) {
         if (!states[s].n_viol) continue;
-        ce = cudaMallocFromPoolAsync((void**)&vbuf[s], 4ull * states[s].n_viol * plans[s].k, pool, st);
-        if (ce != cudaSuccess) {
-            cudaGetLastError();
-            set_error(GFD_ERR_OUT_OF_MEMORY, "violation list: %s", cudaGetErrorString(ce));
-            return GFD_ERR_OUT_OF_MEMORY;
-        }
+        void* p = nullptr;
+        if (int rc = pool_alloc(pool, 4ull * states[s].n_viol * G.plans[s].k, st, &p, "violation list")) return rc;
+        vbuf[s] = (int32_t*)p;
     }
     if (hs.varena_used) {
-        GFD_CUDA(cudaMemcpyAsync(base + off_vptr, vbuf.data(), sizeof(int32_t*) * n, cudaMemcpyHostToDevice, st));
-        GFD_CUDA(cudaMemsetAsync(base + off_vcur, 0, 8ull * n, st));
-        if (int rc = launch_split(A.slots, sched.varena, hs.varena_used, vstride, (int32_t* const*)(base + off_vptr),
-                                  (unsigned long long*)(base + off_vcur), st))
-            return rc;
+        GFD_CUDA(cudaMemcpyAsync(T.vptr, vbuf.data(), sizeof(int32_t*) * n, cudaMemcpyHostToDevice, st));
+        GFD_CUDA(cudaMemsetAsync(T.vcur, 0, 8ull * n, st));
+        if (int rc = launch_split(T.desc, T.varena, hs.varena_used, T.vstride, T.vptr, T.vcur, st)) return rc;
     }
     for (int s = 0; s < n; s++) {
-        gfd_result* r = new gfd_result();
-        r->k = plans[s].k;
-        r->n_matches = states[s].n_matches;
-        r->n_viol = states[s].n_viol;
-        r->d_viol = vbuf[s];
+        gfd_result* r = make_result(G.plans[s], states[s], hs.steps, hs.probes, vbuf[s], st);
         vbuf[s] = nullptr;
-        r->stream = st;
         for (int w = 0; w < 5; w++) {
             r->prof_ms[w] = prof.ms(w);
             r->prof_launch[w] = launches[w];
         }
-        r->stat[0] = hs.steps;
-        r->stat[1] = states[s].st_work;
-        r->stat[2] = states[s].st_rows;
-        r->stat[3] = hs.probes;
-        uint64_t nc = 0;
-        for (int i = 0; i < plans[s].k; i++) nc += states[s].ncand[i];
-        r->stat[4] = nc;
-        r->stat[5] = states[s].st_cpi;
         out[s] = r;
     }
     return GFD_OK;
 }
 
-// ---------------------------------------------------------------- result sort
+// ------------------------------------------------------------------ serving
+namespace {
+
+struct Request {
+    int64_t id = -1;
+    // an owned copy of the GFD
+    std::vector<int32_t> node_label, esrc, edst, elabel;
+    std::vector<gfd_literal> X, Y;
+    gfd_gfd phi{};
+    void fix() {
+        phi.node_label = node_label.data();
+        phi.esrc = esrc.data();
+        phi.edst = edst.data();
+        phi.elabel = elabel.data();
+        phi.X = X.data();
+        phi.Y = Y.data();
+    }
+};
+
+struct SlotHost {
+    bool busy = false;
+    int64_t id = -1;
+    std::shared_ptr<Group> group;
+    int index = 0;  // position inside the group
+    int32_t* viol = nullptr;
+    uint64_t viol_cap = 0;
+    std::unique_ptr<Request> req;
+};
+
+}  // namespace
+
+}  // namespace gfd
+
+struct gfd_session {
+    gfd_graph* g = nullptr;
+    gfd_opts opts{};
+    cudaStream_t st = nullptr;
+    cudaMemPool_t pool = nullptr;
+    gfd::Tables T;
+    int block_threads = 256;
+    int64_t budget = 0;     // device bytes for the workspaces of running requests
+    int64_t used = 0;
+    uint64_t viol_cap = 0;  // violations stored per request before it is run again alone
+    int32_t steps_per_round = 8;
+    std::vector<gfd::SlotHost> slots;
+    std::deque<std::unique_ptr<gfd::Request>> queue;
+    std::deque<std::pair<int64_t, gfd_result*>> done;
+    int64_t next_id = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace gfd {
+
+int session_create(gfd_graph* g, int32_t max_slots, const gfd_opts* o, gfd_session** out) {
+    if (!g || !out || max_slots < 1 || max_slots > 4096) {
+        set_error(GFD_ERR_INVALID_ARG, "gfd_session_create: bad argument");
+        return GFD_ERR_INVALID_ARG;
+    }
+    auto S = std::make_unique<gfd_session>();
+    S->g = g;
+    if (o) S->opts = *o;
+    S->st = o && o->cuda_stream ? (cudaStream_t)o->cuda_stream : g->stream;
+    S->block_threads = (o && o->block_threads == 512) ? 512 : 256;
+    S->budget = default_budget(o);
+    S->viol_cap = o && o->max_violations_hint > 0 ? (uint64_t)o->max_violations_hint : (1ull << 20);
+    S->slots.resize(max_slots);
+    if (int rc = get_pool(g, &S->pool)) return rc;
+    if (int rc = tables_alloc(S->pool, max_slots, S->block_threads, 0, 0, false, S->st, &S->T)) return rc;
+    if (int rc = mark_idle(S->T.state, max_slots, S->st)) return rc;  // every slot starts idle
+    // the enumeration steps of one round, captured once (the tables never move)
+    const EnumArgs A = enum_args(g, S->T);
+    if (int rc = capture_steps(A, S->block_threads, S->steps_per_round, S->st, &S->graph, &S->exec)) return rc;
+    GFD_CUDA(cudaStreamSynchronize(S->st));
+    *out = S.release();
+    return GFD_OK;
+}
+
+void session_free(gfd_session* S) {
+    if (!S) return;
+    cudaStreamSynchronize(S->st);
+    for (auto& d : S->done) gfd_result_free(d.second);
+    for (auto& sl : S->slots) {
+        if (sl.viol) cudaFreeAsync(sl.viol, S->st);
+        if (sl.group && --sl.group->live == 0 && sl.group->base) cudaFreeAsync(sl.group->base, S->st);
+        sl.group.reset();
+    }
+    if (S->T.base) cudaFreeAsync(S->T.base, S->st);
+    if (S->exec) cudaGraphExecDestroy(S->exec);
+    if (S->graph) cudaGraphDestroy(S->graph);
+    cudaStreamSynchronize(S->st);
+    delete S;
+}
+
+int session_submit(gfd_session* S, const gfd_gfd* phi, int64_t* id) {
+    if (!S || !phi || !id) {
+        set_error(GFD_ERR_INVALID_ARG, "gfd_session_submit: NULL argument");
+        return GFD_ERR_INVALID_ARG;
+    }
+    // plan now so that an invalid GFD is reported at submission
+    HostPlan P;
+    if (int rc = make_plan(phi, S->g->n_attrs, S->g->plan_stats(), &P)) return rc;
+    auto R = std::make_unique<Request>();
+    R->id = S->next_id++;
+    R->node_label.assign(phi->node_label, phi->node_label + phi->k);
+    for (int e = 0; e < phi->m; e++) {
+        R->esrc.push_back(phi->esrc[e]);
+        R->edst.push_back(phi->edst[e]);
+        R->elabel.push_back(phi->elabel[e]);
+    }
+    if (phi->nx) R->X.assign(phi->X, phi->X + phi->nx);
+    if (!phi->y_false && phi->ny) R->Y.assign(phi->Y, phi->Y + phi->ny);
+    R->phi = *phi;
+    R->phi.ny = phi->y_false ? 0 : phi->ny;
+    R->fix();
+    *id = R->id;
+    S->queue.push_back(std::move(R));
+    return GFD_OK;
+}
+
+namespace {
+
+// Admit queued requests, in arrival order, while a slot is free and their
+// device memory (workspace and violation buffer) fits the budget; the admitted
+// ones are planned and indexed together as one group.
+int session_admit(gfd_session* S) {
+    std::vector<int> free_slots;
+    for (int i = 0; i < (int)S->slots.size(); i++)
+        if (!S->slots[i].busy) free_slots.push_back(i);
+    if (free_slots.empty() || S->queue.empty()) return GFD_OK;
+    const int64_t per_slot = S->budget / (int64_t)S->slots.size();
+    std::vector<std::unique_ptr<Request>> take;
+    std::vector<const gfd_gfd*> phis;
+    int64_t need = 0;
+    while (!S->queue.empty() && take.size() < free_slots.size()) {
+        Request* R = S->queue.front().get();
+        Group trial;
+        const gfd_gfd* one[1] = {&R->phi};
+        if (int rc = group_plan(S->g, one, 1, &S->opts, per_slot, &trial)) return rc;
+        const int64_t req_bytes = (int64_t)trial.bytes + (int64_t)(4ull * trial.plans[0].k * S->viol_cap);
+        const bool idle = S->used == 0 && take.empty();  // always admit into an idle device
+        if (!idle && S->used + need + req_bytes > S->budget) break;
+        need += req_bytes;
+        phis.push_back(&R->phi);
+        take.push_back(std::move(S->queue.front()));
+        S->queue.pop_front();
+    }
+    if (take.empty()) return GFD_OK;
+    const int n = (int)take.size();
+    auto G = std::make_shared<Group>();
+    if (int rc = group_plan(S->g, phis.data(), n, &S->opts, per_slot, G.get())) return rc;
+    void* wb = nullptr;
+    if (int rc = pool_alloc(S->pool, G->bytes, S->st, &wb, "request workspace")) return rc;
+    G->base = (uint8_t*)wb;
+    G->slot.assign(free_slots.begin(), free_slots.begin() + n);
+    S->used += (int64_t)G->bytes;
+    for (int i = 0; i < n; i++) {
+        void* vp = nullptr;
+        if (int rc = pool_alloc(S->pool, 4ull * G->plans[i].k * S->viol_cap, S->st, &vp, "violation buffer")) return rc;
+        G->descs[i].viol = (int32_t*)vp;
+        G->descs[i].viol_cap = S->viol_cap;
+        S->used += (int64_t)(4ull * G->plans[i].k * S->viol_cap);
+        SlotHost& sl = S->slots[G->slot[i]];
+        sl.busy = true;
+        sl.id = take[i]->id;
+        sl.group = G;
+        sl.index = i;
+        sl.viol = (int32_t*)vp;
+        sl.viol_cap = S->viol_cap;
+        sl.req = std::move(take[i]);
+    }
+    G->live = n;
+    const bool refine = !(S->opts.flags & GFD_FLAG_NO_REFINE);
+    if (int rc = group_build(S->g, G.get(), S->T, refine, S->st)) return rc;
+    ProfEvents prof;
+    int64_t launches[5] = {0, 0, 0, 0, 0};
+    if (int rc = group_launch(S->g, G.get(), S->T, S->st, prof, launches)) return rc;
+    return init_slots(enum_args(S->g, S->T), G->slot.data(), n, S->st);
+}
+
+}  // namespace
+
+int session_step(gfd_session* S, int32_t* n_running, int32_t* n_queued) {
+    if (!S) {
+        set_error(GFD_ERR_INVALID_ARG, "gfd_session_step: NULL session");
+        return GFD_ERR_INVALID_ARG;
+    }
+    if (int rc = session_admit(S)) return rc;
+    int busy = 0;
+    for (auto& sl : S->slots) busy += sl.busy;
+    if (busy) {
+        GFD_CUDA(cudaGraphLaunch(S->exec, S->st));
+        std::vector<SlotState> states(S->slots.size());
+        Sched hs{};
+        int32_t herr = 0;
+        GFD_CUDA(cudaMemcpyAsync(states.data(), S->T.state, sizeof(SlotState) * states.size(), cudaMemcpyDeviceToHost,
+                                 S->st));
+        GFD_CUDA(cudaMemcpyAsync(&hs, S->T.sched, sizeof(Sched), cudaMemcpyDeviceToHost, S->st));
+        GFD_CUDA(cudaMemcpyAsync(&herr, S->T.err, sizeof(int32_t), cudaMemcpyDeviceToHost, S->st));
+        GFD_CUDA(cudaStreamSynchronize(S->st));
+        if (hs.err == DERR_TIMEOUT) {
+            set_error(GFD_ERR_TIMEOUT, "a device-side limit ran out in the serving session");
+            return GFD_ERR_TIMEOUT;
+        }
+        if (herr) {
+            set_error(GFD_ERR_OVERFLOW, "index capacity exceeded");
+            return GFD_ERR_OVERFLOW;
+        }
+        for (size_t i = 0; i < S->slots.size(); i++) {
+            SlotHost& sl = S->slots[i];
+            if (!sl.busy || states[i].cur >= 0) continue;
+            if (states[i].err) {
+                set_error(GFD_ERR_OVERFLOW, "request %lld: partial-match counter overflow", (long long)sl.id);
+                return GFD_ERR_OVERFLOW;
+            }
+            gfd_result* r = nullptr;
+            if (states[i].n_viol > sl.viol_cap) {
+                // more violations than the request's buffer holds: validate it again alone
+                gfd_opts o2 = S->opts;
+                o2.cuda_stream = S->st;
+                o2.flags &= ~GFD_FLAG_HOST_LOOP;
+                o2.max_violations_hint = (int64_t)states[i].n_viol;
+                const gfd_gfd* one[1] = {&sl.req->phi};
+                if (int rc = run_batch(S->g, one, 1, &o2, &r)) return rc;
+                r->stat[6] += 1;
+                cudaFreeAsync(sl.viol, S->st);
+            } else {
+                r = make_result(sl.group->plans[sl.index], states[i], hs.steps, hs.probes, sl.viol, S->st);
+            }
+            sl.viol = nullptr;
+            S->done.emplace_back(sl.id, r);
+            S->used -= (int64_t)(4ull * sl.group->plans[sl.index].k * sl.viol_cap);
+            if (--sl.group->live == 0) {
+                cudaFreeAsync(sl.group->base, S->st);
+                S->used -= (int64_t)sl.group->bytes;
+                sl.group->base = nullptr;
+            }
+            sl.group.reset();
+            sl.req.reset();
+            sl.busy = false;
+            sl.id = -1;
+        }
+    }
+    int running = 0;
+    for (auto& sl : S->slots) running += sl.busy;
+    if (n_running) *n_running = running;
+    if (n_queued) *n_queued = (int32_t)S->queue.size();
+    return GFD_OK;
+}
+
+int session_next_result(gfd_session* S, int64_t* id, gfd_result** out) {
+    if (!S || !id || !out) {
+        set_error(GFD_ERR_INVALID_ARG, "gfd_session_next_result: NULL argument");
+        return GFD_ERR_INVALID_ARG;
+    }
+    if (S->done.empty()) {
+        *id = -1;
+        *out = nullptr;
+        return GFD_OK;
+    }
+    *id = S->done.front().first;
+    *out = S->done.front().second;
+    S->done.pop_front();
+    return GFD_OK;
+}
+
+// ------------------------------------------------------------------ result sort
 namespace {
 
 __global__ void k_iota(uint32_t* p, uint64_t n) {

@@ -191,3 +191,19 @@ def kg(scale: int = 1) -> tuple[Graph, list[GFD]]:
                        gamma_out=2.28, gamma_in=2.5,
                        out_cap_frac=min(1.0, 1e6 / (KG_E // scale)), name="kg")
     return g, kg_gfds()
+
+
+# ------------------------------------------------------------------------ serving
+SERVE_RATES = (50, 200, 500, 1000, 2000)
+
+
+def serving_requests(graph: Graph, n: int, seed_index: int = 4) -> list[GFD]:
+    """Single-GFD requests drawn like the batched GFDs (3-8 nodes, 1-4 literals)
+    with their own seed."""
+    return batched_gfds(graph, n, seed_index=seed_index)
+
+
+def poisson_arrivals(rate: float, n: int, seed: int = 0) -> np.ndarray:
+    """Arrival times (seconds from 0) of n requests of a Poisson process."""
+    rng = _rng(4, 1000 + seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=n))
