@@ -225,6 +225,11 @@ def main():
     ap.add_argument("--flags", type=int, default=0)
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="frontier budget in GiB (0: the library default)")
+    ap.add_argument("--hint", type=int, default=1 << 26,
+                    help="violation records stored per call before a re-run")
+    ap.add_argument("--serve-rates", default="200,1000,2000",
+                    help="Poisson arrival rates (req/s) of the serving leg; empty: skip")
+    ap.add_argument("--serve-requests", type=int, default=256)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -255,7 +260,7 @@ def main():
     stream = torch.cuda.current_stream()
     dg = G.Graph(g, stream=stream)
     flags = G.FLAG_PROFILE | args.flags
-    hint = 1 << 26   # violation records stored per call (all GFDs together)
+    hint = args.hint   # violation records stored per call (all GFDs together)
     l2_flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
     budget = int(args.budget_gb * (1 << 30))
@@ -360,6 +365,27 @@ def main():
         plain = {"value": pm / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms,
                  "launch": f"{len(qs)} gfd_validate calls per step"}
 
+    # serving: a Poisson stream of single-GFD requests against the resident
+    # graph, continuous batching vs one gfd_validate per request
+    serving = None
+    rates = [float(x) for x in args.serve_rates.split(",") if x.strip()]
+    if rates and args.workload == "batched":
+        from synth import configs
+        from paper_2608_02321_gb300 import serving as srv
+        reqs = configs.serving_requests(g, args.serve_requests)
+        serving = {"requests_per_rate": len(reqs), "max_slots": 64, "budget_gb": 40}
+        for lam in rates:
+            arr = configs.poisson_arrivals(lam, len(reqs), seed=int(lam))
+            torch.cuda.synchronize()
+            cont, _ = srv.serve(dg, reqs, arr, max_slots=64, budget_bytes=40 << 30, stream=stream)
+            torch.cuda.synchronize()
+            ser = srv.serve_serial(dg, reqs, arr, stream=stream)
+            serving[f"rate_{int(lam)}"] = {
+                "continuous": {k: cont[k] for k in ("p50_ms", "p99_ms", "matches_per_s", "requests_per_s",
+                                                    "makespan_s", "peak_running")},
+                "serial_plain": {k: ser[k] for k in ("p50_ms", "p99_ms", "matches_per_s", "requests_per_s",
+                                                     "makespan_s")}}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = cpu_threads()
@@ -376,7 +402,7 @@ def main():
                                                   "every timed step",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "plain": plain,
+                "clocks": clk, "plain": plain, "serving": serving,
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,
                 "matches_per_step": matches, "violations_per_step": viols,
                 "work_items_per_step": work, "edge_probes_per_step": probes,
