@@ -230,6 +230,7 @@ def main():
     ap.add_argument("--serve-rates", default="200,1000,2000",
                     help="Poisson arrival rates (req/s) of the serving leg; empty: skip")
     ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--n-gfds", type=int, default=0, help="validate only the first N GFDs (profiling)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -257,6 +258,9 @@ def main():
     import paper_2608_02321_gb300 as G
     G.load_library(build_if_missing=False)
     g, qs, desc = make_workload(args.workload, args.scale)
+    if args.n_gfds:
+        qs = qs[:args.n_gfds]
+        desc += f" (first {len(qs)} GFDs only)"
     stream = torch.cuda.current_stream()
     dg = G.Graph(g, stream=stream)
     flags = G.FLAG_PROFILE | args.flags

@@ -38,6 +38,7 @@ namespace gfd {
 namespace {
 
 constexpr int CTRL_THREADS = 1024;
+constexpr uint64_t LAST_LEVEL_CHUNK = 1ull << 25;  // work items per step at the last level
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
@@ -426,7 +427,11 @@ __device__ void control_step(const EnumArgs& A, bool first) {
             if (S->cur >= 0) {
                 const int l = S->cur;
                 S->cb = S->cursor[l];
-                S->ce = min(S->cb + D->chunk, S->total[l]);
+                // the last level writes no partial matches, so its steps are not
+                // bounded by the row buffers
+                const bool to_last = k == 1 || l + 1 == k - 1;
+                const uint64_t step = to_last ? max(D->chunk, (uint64_t)LAST_LEVEL_CHUNK) : D->chunk;
+                S->ce = min(S->cb + step, S->total[l]);
                 if (k > 1 && l + 1 <= k - 2) S->ctr[l + 1] = 0;
                 tiles = (uint32_t)((S->ce - S->cb + A.tile - 1) / A.tile);
                 S->st_work += S->ce - S->cb;

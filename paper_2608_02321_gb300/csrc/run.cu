@@ -233,6 +233,20 @@ struct Group {
 
 namespace {
 
+// Top-down constraint "x in C(i) needs a neighbour in C(q) through an edge
+// leaving x (dir 1) or entering x (dir 0)": scattering from C(q) scans the
+// opposite-direction adjacency of the q label class; gathering scans the
+// dir-direction adjacency of the i label class but stops at the first hit
+// (counted as half of it).
+bool td_gather_cheaper(const gfd_graph* g, int32_t label_q, int32_t label_i, int dir) {
+    auto degsum = [&](int32_t L, bool out) -> double {
+        return L == GFD_WILDCARD ? (double)g->m : (double)g->label_stats[3 * (size_t)L + (out ? 1 : 2)];
+    };
+    const double scatter = degsum(label_q, dir == 0);
+    const double gather = 0.5 * degsum(label_i, dir == 1);
+    return gather < scatter;
+}
+
 // Plans, capacities and the workspace layout of a group (host only).
 int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* o, int64_t frontier_per_slot,
                Group* G) {
@@ -322,8 +336,9 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
         for (int i = 0; i < P.k; i++) {
             n_sct += refine ? P.td[i].size() : 0;
             const bool pr = refine && !P.bu[i].empty();
-            n_prn += pr;
-            n_compact += pr;
+            const bool tdg = refine && !P.td[i].empty();  // at most one top-down gather per level
+            n_prn += pr + tdg;
+            n_compact += pr + tdg;
         }
     }
     G->cmp_chunks = compact_chunks(g->dg);
@@ -398,17 +413,35 @@ int group_build(gfd_graph* g, Group* G, const Tables& T, bool refine, cudaStream
         G->phases.push_back({0, a0, G->and_jobs.size() - a0});
         G->phases.push_back({1, c0, G->compact_jobs.size() - c0});
     } else {
-        // top-down, level by level
+        // top-down, level by level. Each constraint from an earlier level is
+        // applied in the cheaper direction: scatter marks from the earlier
+        // level's candidates (cost ~ their degree sum), or, after compaction,
+        // keep the level's own candidates that have a neighbour there
+        // (a gather that stops at the first hit).
         for (int lvl = 0; lvl < maxk; lvl++) {
             size_t a0 = G->and_jobs.size(), c0 = G->compact_jobs.size(), s0 = G->scatter_jobs.size();
+            size_t p0 = G->prune_jobs.size();
             size_t tmp_used = 0;
+            std::vector<int> gathered;
             for (int s = 0; s < n; s++) {
                 const HostPlan& P = G->plans[s];
                 if (lvl >= P.k) continue;
                 AndJob J{};
                 J.bm = G->descs[s].bm[lvl];
                 J.src = keybm(G->slot_key[s][lvl]);
+                PruneJob Pj{};
+                Pj.cand = G->descs[s].cand[lvl];
+                Pj.count = state_ncand(s, lvl);
+                Pj.bm = G->descs[s].bm[lvl];
                 for (const Con& c : P.td[lvl]) {
+                    const int32_t lq = G->plans[s].key[c.q].label, li = G->plans[s].key[lvl].label;
+                    if (td_gather_cheaper(g, lq, li, c.dir)) {
+                        Pj.con_bm[Pj.ncon] = G->descs[s].bm[c.q];
+                        Pj.con_dir[Pj.ncon] = c.dir;
+                        Pj.con_lab[Pj.ncon] = c.lab;
+                        Pj.ncon++;
+                        continue;
+                    }
                     uint32_t* marks = (uint32_t*)(base + G->o_tmp + 4ull * nwords * tmp_used++);
                     ScatterJob S{};
                     S.qcand = G->descs[s].cand[c.q];
@@ -423,11 +456,21 @@ int group_build(gfd_graph* g, Group* G, const Tables& T, bool refine, cudaStream
                 }
                 G->and_jobs.push_back(J);
                 G->compact_jobs.push_back(compact_job(s, lvl));
+                if (Pj.ncon) {
+                    G->prune_jobs.push_back(Pj);
+                    gathered.push_back(s);
+                }
             }
             if (tmp_used) G->phases.push_back({4, 0, tmp_used});
             if (G->scatter_jobs.size() > s0) G->phases.push_back({2, s0, G->scatter_jobs.size() - s0});
             G->phases.push_back({0, a0, G->and_jobs.size() - a0});
             G->phases.push_back({1, c0, G->compact_jobs.size() - c0});
+            if (!gathered.empty()) {
+                const size_t c1 = G->compact_jobs.size();
+                for (int s : gathered) G->compact_jobs.push_back(compact_job(s, lvl));
+                G->phases.push_back({3, p0, G->prune_jobs.size() - p0});
+                G->phases.push_back({1, c1, G->compact_jobs.size() - c1});
+            }
         }
         // bottom-up, reverse level order
         for (int lvl = maxk - 1; lvl >= 0; lvl--) {
