@@ -207,8 +207,10 @@ int gfd_session_create(const gfd_graph *g, int32_t max_slots, const gfd_opts *op
  * checked here: an invalid one is rejected with the usual error codes. */
 int gfd_session_submit(gfd_session *s, const gfd_gfd *phi, int64_t *request_id);
 /* Admit, run one round of enumeration steps, collect finished requests.
- * *n_running and *n_queued (may be NULL) report the occupancy afterwards. */
-int gfd_session_step(gfd_session *s, int32_t *n_running, int32_t *n_queued);
+ * *n_advanced: requests that ran together in this round; *n_running and
+ * *n_queued: requests still running and still waiting afterwards (any of the
+ * three may be NULL). */
+int gfd_session_step(gfd_session *s, int32_t *n_advanced, int32_t *n_running, int32_t *n_queued);
 /* Pop one finished request: *request_id = -1 and *out = NULL when none is
  * ready. The caller owns *out (gfd_result_free). */
 int gfd_session_next_result(gfd_session *s, int64_t *request_id, gfd_result **out);

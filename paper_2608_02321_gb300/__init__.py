@@ -86,7 +86,7 @@ _SIGS = {
     "gfd_result_free": (None, [C.c_void_p]),
     "gfd_session_create": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(gfd_opts), C.POINTER(C.c_void_p)]),
     "gfd_session_submit": (C.c_int, [C.c_void_p, C.POINTER(gfd_gfd), C.POINTER(C.c_int64)]),
-    "gfd_session_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "gfd_session_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "gfd_session_next_result": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_void_p)]),
     "gfd_session_free": (None, [C.c_void_p]),
     "gfd_node_candidates_noalloc": (C.c_int, [C.c_void_p, C.POINTER(gfd_gfd), C.c_int32, C.c_void_p,
@@ -312,11 +312,13 @@ class Session:
         return int(rid.value)
 
     def step(self):
-        """(running, queued) after one admission + enumeration round."""
+        """One admission + enumeration round: (requests that advanced together
+        in it, requests still running, requests still queued)."""
+        a = C.c_int32(0)
         r = C.c_int32(0)
         q = C.c_int32(0)
-        _check(_lib.gfd_session_step(self._h, C.byref(r), C.byref(q)))
-        return int(r.value), int(q.value)
+        _check(_lib.gfd_session_step(self._h, C.byref(a), C.byref(r), C.byref(q)))
+        return int(a.value), int(r.value), int(q.value)
 
     def results(self):
         """All finished requests since the last call: [(request_id, Result)]."""

@@ -105,8 +105,8 @@ int gfd_session_submit(gfd_session* s, const gfd_gfd* phi, int64_t* request_id) 
     return gfd::session_submit(s, phi, request_id);
 }
 
-int gfd_session_step(gfd_session* s, int32_t* n_running, int32_t* n_queued) {
-    return gfd::session_step(s, n_running, n_queued);
+int gfd_session_step(gfd_session* s, int32_t* n_advanced, int32_t* n_running, int32_t* n_queued) {
+    return gfd::session_step(s, n_advanced, n_running, n_queued);
 }
 
 int gfd_session_next_result(gfd_session* s, int64_t* request_id, gfd_result** out) {

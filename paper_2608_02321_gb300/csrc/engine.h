@@ -142,7 +142,7 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
 int session_create(gfd_graph* g, int32_t max_slots, const gfd_opts* o, gfd_session** out);
 void session_free(gfd_session* s);
 int session_submit(gfd_session* s, const gfd_gfd* phi, int64_t* id);
-int session_step(gfd_session* s, int32_t* n_running, int32_t* n_queued);
+int session_step(gfd_session* s, int32_t* n_advanced, int32_t* n_running, int32_t* n_queued);
 int session_next_result(gfd_session* s, int64_t* id, gfd_result** out);
 int result_fetch(gfd_result* r);
 

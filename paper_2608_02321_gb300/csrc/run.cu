@@ -903,7 +903,7 @@ int session_admit(gfd_session* S) {
 
 }  // namespace
 
-int session_step(gfd_session* S, int32_t* n_running, int32_t* n_queued) {
+int session_step(gfd_session* S, int32_t* n_advanced, int32_t* n_running, int32_t* n_queued) {
     if (!S) {
         set_error(GFD_ERR_INVALID_ARG, "gfd_session_step: NULL session");
         return GFD_ERR_INVALID_ARG;
@@ -911,6 +911,7 @@ int session_step(gfd_session* S, int32_t* n_running, int32_t* n_queued) {
     if (int rc = session_admit(S)) return rc;
     int busy = 0;
     for (auto& sl : S->slots) busy += sl.busy;
+    if (n_advanced) *n_advanced = busy;
     if (busy) {
         GFD_CUDA(cudaGraphLaunch(S->exec, S->st));
         std::vector<SlotState> states(S->slots.size());

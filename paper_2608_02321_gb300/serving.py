@@ -53,8 +53,8 @@ def serve(g: Graph, gfds, arrivals, max_slots: int = 64, budget_bytes: int = 40 
             i += 1
         outstanding = len(owner) - sum(1 for j in owner.values() if finish[j])
         if outstanding:
-            running, queued = s.step()
-            peak_running = max(peak_running, running)
+            advanced, running, queued = s.step()
+            peak_running = max(peak_running, advanced)
         else:
             running = queued = 0
         done_now = s.results()
