@@ -35,8 +35,8 @@ def test_session_results_equal_alone(setup):
         for q in burst:
             ids[s.submit(q)] = len(ids)
         for _ in range(3):
-            running, queued = s.step()
-            peak = max(peak, running)
+            advanced, running, queued = s.step()
+            peak = max(peak, advanced)
             for rid, res in s.results():
                 got[ids[rid]] = (res.n_matches, res.violations())
     while len(got) < len(reqs):
