@@ -231,6 +231,7 @@ def main():
                     help="Poisson arrival rates (req/s) of the serving leg; empty: skip")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--n-gfds", type=int, default=0, help="validate only the first N GFDs (profiling)")
+    ap.add_argument("--no-autotune", action="store_true", help="skip gfd_autotune before the warm-up")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -273,6 +274,11 @@ def main():
         return dg.validate_batch(qs, stream=stream, flags=flags, max_violations_hint=hint,
                                  frontier_budget_bytes=budget)
 
+    tuned = None
+    if not args.no_autotune:
+        # untimed: pick the enumeration-kernel variant and frontier budget
+        tuned = dg.autotune(qs, stream=stream, max_violations_hint=hint,
+                            frontier_budget_bytes=budget)
     for _ in range(args.warmup):
         res = step()
     torch.cuda.synchronize()
@@ -406,7 +412,7 @@ def main():
                                                   "every timed step",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "plain": plain, "serving": serving,
+                "clocks": clk, "plain": plain, "serving": serving, "autotuned": tuned,
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,
                 "matches_per_step": matches, "violations_per_step": viols,
                 "work_items_per_step": work, "edge_probes_per_step": probes,

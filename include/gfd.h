@@ -132,7 +132,11 @@ typedef struct {
 typedef struct {
     int64_t frontier_budget_bytes; /* device bytes for partial-match buffers */
     int32_t chunk_rows;            /* partial matches expanded per step and GFD */
-    int32_t block_threads;         /* threads per block of the expansion kernel */
+    int32_t kernel_variant;        /* enumeration kernel: 0 = the graph's tuned
+                                      choice (gfd_autotune) or the default;
+                                      1..6 = a fixed variant (threads per block
+                                      and minimum resident blocks per SM:
+                                      256/4, 256/6, 256/8, 128/12, 128/16, 512/3) */
     int64_t max_violations_hint;   /* violations the run stores before it must
                                       run again with exactly enough room (all
                                       GFDs of a call together) */
@@ -146,6 +150,16 @@ int gfd_graph_load(const gfd_graph_desc *desc, const gfd_opts *opts, gfd_graph *
 
 /* Release a graph handle and its device memory. */
 void gfd_graph_free(gfd_graph *g);
+
+/* Autotuner: validate the batch phis[0..n) once per enumeration-kernel variant
+ * and frontier budget (the budget of opts, or the default, and a quarter of
+ * it), time the device work of each run with CUDA events, and keep the
+ * fastest choice in the graph handle, where later calls with kernel_variant 0
+ * and no frontier budget of their own use it. *best (may be NULL) receives
+ * opts with the chosen kernel_variant and frontier_budget_bytes. The results
+ * of the trial runs are discarded. */
+int gfd_autotune(gfd_graph *g, const gfd_gfd *const *phis, int32_t n, const gfd_opts *opts,
+                 gfd_opts *best);
 
 /* Vertex count, edge count and resident device bytes of a loaded graph. */
 int32_t gfd_graph_vertices(const gfd_graph *g);

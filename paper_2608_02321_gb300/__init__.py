@@ -63,7 +63,7 @@ class gfd_gfd(C.Structure):
 
 class gfd_opts(C.Structure):
     _fields_ = [("frontier_budget_bytes", C.c_int64), ("chunk_rows", C.c_int32),
-                ("block_threads", C.c_int32), ("max_violations_hint", C.c_int64),
+                ("kernel_variant", C.c_int32), ("max_violations_hint", C.c_int64),
                 ("cuda_stream", C.c_void_p), ("flags", C.c_int32)]
 
 
@@ -77,6 +77,8 @@ _SIGS = {
     "gfd_validate": (C.c_int, [C.c_void_p, C.POINTER(gfd_gfd), C.POINTER(gfd_opts), C.POINTER(C.c_void_p)]),
     "gfd_validate_batch": (C.c_int, [C.c_void_p, C.POINTER(C.POINTER(gfd_gfd)), C.c_int32,
                                      C.POINTER(gfd_opts), C.POINTER(C.c_void_p)]),
+    "gfd_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.POINTER(gfd_gfd)), C.c_int32, C.POINTER(gfd_opts),
+                              C.POINTER(gfd_opts)]),
     "gfd_result_matches": (C.c_uint64, [C.c_void_p]),
     "gfd_result_violations": (C.c_uint64, [C.c_void_p]),
     "gfd_result_arity": (C.c_int32, [C.c_void_p]),
@@ -147,12 +149,12 @@ def _stream_handle(stream):
     return int(getattr(stream, "cuda_stream"))   # torch.cuda.Stream
 
 
-def make_opts(frontier_budget_bytes=0, chunk_rows=0, block_threads=0, max_violations_hint=0,
+def make_opts(frontier_budget_bytes=0, chunk_rows=0, kernel_variant=0, max_violations_hint=0,
               stream=None, flags=0) -> gfd_opts:
     o = gfd_opts()
     o.frontier_budget_bytes = int(frontier_budget_bytes)
     o.chunk_rows = int(chunk_rows)
-    o.block_threads = int(block_threads)
+    o.kernel_variant = int(kernel_variant)
     o.max_violations_hint = int(max_violations_hint)
     o.cuda_stream = _stream_handle(stream)
     o.flags = int(flags)
@@ -278,6 +280,17 @@ class Graph:
         h = C.c_void_p(None)
         _check(_lib.gfd_validate(self._h, C.byref(b.s), C.byref(o), C.byref(h)))
         return Result(h)
+
+    def autotune(self, gfds, **opts) -> dict:
+        """Time the enumeration-kernel variants and frontier budgets on this
+        batch (gfd_autotune) and keep the fastest for later calls."""
+        o = make_opts(**opts)
+        bufs = [_GfdBuf(g) for g in gfds]
+        arr = (C.POINTER(gfd_gfd) * max(1, len(bufs)))(*[C.pointer(b.s) for b in bufs])
+        best = gfd_opts()
+        _check(_lib.gfd_autotune(self._h, arr, len(bufs), C.byref(o), C.byref(best)))
+        return {"kernel_variant": int(best.kernel_variant),
+                "frontier_budget_bytes": int(best.frontier_budget_bytes)}
 
     def validate_batch(self, gfds, **opts) -> list:
         o = make_opts(**opts)

@@ -64,6 +64,15 @@ int gfd_validate_batch(const gfd_graph* g, const gfd_gfd* const* phis, int32_t n
     return gfd::run_batch(gm, phis, n, opts, out);
 }
 
+int gfd_autotune(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opts* opts, gfd_opts* best) {
+    if (!g) {
+        gfd::set_error(GFD_ERR_INVALID_ARG, "gfd_autotune: NULL graph");
+        return GFD_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g->mu);
+    return gfd::autotune(g, phis, n, opts, best);
+}
+
 uint64_t gfd_result_matches(const gfd_result* r) { return r ? r->n_matches : 0; }
 uint64_t gfd_result_violations(const gfd_result* r) { return r ? r->n_viol : 0; }
 int32_t gfd_result_arity(const gfd_result* r) { return r ? r->k : 0; }

@@ -36,6 +36,8 @@ struct gfd_graph {
     cudaStream_t stream = nullptr;
     gfd::Engine* eng = nullptr;
     std::mutex mu;
+    int32_t tuned_variant = -1;          // set by gfd_autotune
+    int64_t tuned_budget = 0;
 };
 
 struct gfd_result {
@@ -124,15 +126,19 @@ int enum_init(const EnumArgs& a, cudaStream_t st);
 int mark_idle(SlotState* state, int n, cudaStream_t st);
 int init_slots(const EnumArgs& a, const int* host_ids, int n, cudaStream_t st);
 // Capture `steps` enumeration steps (expand + control) into a CUDA graph.
-int capture_steps(const EnumArgs& a, int block_threads, int steps, cudaStream_t st, cudaGraph_t* graph,
+int capture_steps(const EnumArgs& a, int variant, int steps, cudaStream_t st, cudaGraph_t* graph,
                   cudaGraphExec_t* exec);
 // Split the violation arena (records [slot, tuple...]) into per-slot lists.
 int launch_split(const SlotDesc* slots, const int32_t* arena, uint64_t n, int32_t stride, int32_t* const* lists,
                  unsigned long long* cursor, cudaStream_t st);
 // Runs supersteps until every slot is finished. persistent: one cooperative
-// launch; else a host loop (optionally captured into CUDA graphs).
-int enum_run(const EnumArgs& a, bool persistent, bool use_graph, int block_threads, cudaStream_t st,
-             cudaEvent_t ev0, cudaEvent_t ev1, int64_t* launches);
+// launch; else a host loop (optionally captured into CUDA graphs). variant:
+// 0 (256 threads, >= 4 blocks/SM), 1 (256, >= 6), 2 (256, >= 8), 3 (128, >= 12),
+// 4 (128, >= 16), 5 (512, >= 3).
+int enum_run(const EnumArgs& a, bool persistent, bool use_graph, int variant, cudaStream_t st, cudaEvent_t ev0,
+             cudaEvent_t ev1, int64_t* launches);
+int variant_threads(int variant);
+constexpr int N_VARIANTS = 6;
 
 // ---- orchestration (run.cu)
 int graph_load(const gfd_graph_desc* d, const gfd_opts* o, gfd_graph** out);
@@ -144,6 +150,7 @@ void session_free(gfd_session* s);
 int session_submit(gfd_session* s, const gfd_gfd* phi, int64_t* id);
 int session_step(gfd_session* s, int32_t* n_advanced, int32_t* n_running, int32_t* n_queued);
 int session_next_result(gfd_session* s, int64_t* id, gfd_result** out);
+int autotune(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opts* o, gfd_opts* best);
 int result_fetch(gfd_result* r);
 
 }  // namespace gfd

@@ -459,8 +459,8 @@ __global__ void __launch_bounds__(CTRL_THREADS) k_control(EnumArgs A, int first)
     control_step<CTRL_THREADS>(A, first != 0);
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) k_expand(EnumArgs A) {
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_expand(EnumArgs A) {
     expand_tiles<NT>(A);
 }
 
@@ -502,8 +502,8 @@ __device__ bool grid_barrier(Sched* s) {
     return ok_s != 0;
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) k_persistent(EnumArgs A) {
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_persistent(EnumArgs A) {
     for (;;) {
         expand_tiles<NT>(A);
         if (!grid_barrier(A.sched)) return;
@@ -513,12 +513,12 @@ __global__ void __launch_bounds__(NT) k_persistent(EnumArgs A) {
     }
 }
 
-template <int NT>
+template <int NT, int MINB>
 int launch_persistent(const EnumArgs& a, cudaStream_t st, int64_t* launches) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<NT>, NT, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<NT, MINB>, NT, 0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm < 1) {
         set_error(GFD_ERR_CUDA, "persistent enumeration kernel cannot be resident");
@@ -527,24 +527,24 @@ int launch_persistent(const EnumArgs& a, cudaStream_t st, int64_t* launches) {
     const int grid = sms * per_sm;
     EnumArgs args = a;
     void* params[] = {&args};
-    e = cudaLaunchCooperativeKernel((const void*)k_persistent<NT>, dim3(grid), dim3(NT), params, 0, st);
+    e = cudaLaunchCooperativeKernel((const void*)k_persistent<NT, MINB>, dim3(grid), dim3(NT), params, 0, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel");
     if (launches) *launches += 1;
     return GFD_OK;
 }
 
-template <int NT>
+template <int NT, int MINB>
 int expand_grid() {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand<NT>, NT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand<NT, MINB>, NT, 0);
     return sms * std::max(per_sm, 1);
 }
 
-template <int NT>
+template <int NT, int MINB>
 int host_loop(const EnumArgs& a, bool use_graph, cudaStream_t st, int64_t* launches) {
-    const int grid = expand_grid<NT>();
+    const int grid = expand_grid<NT, MINB>();
     int32_t* h_active = nullptr;
     cudaError_t e = cudaMallocHost(&h_active, sizeof(int32_t));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
@@ -556,7 +556,7 @@ int host_loop(const EnumArgs& a, bool use_graph, cudaStream_t st, int64_t* launc
         e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             for (int it = 0; it < per_check; it++) {
-                k_expand<NT><<<grid, NT, 0, st>>>(a);
+                k_expand<NT, MINB><<<grid, NT, 0, st>>>(a);
                 k_control<<<1, CTRL_THREADS, 0, st>>>(a, 0);
             }
             e = cudaStreamEndCapture(st, &graph);
@@ -574,7 +574,7 @@ int host_loop(const EnumArgs& a, bool use_graph, cudaStream_t st, int64_t* launc
             if (launches) *launches += 2 * per_check;
         } else {
             for (int it = 0; it < per_check; it++) {
-                k_expand<NT><<<grid, NT, 0, st>>>(a);
+                k_expand<NT, MINB><<<grid, NT, 0, st>>>(a);
                 k_control<<<1, CTRL_THREADS, 0, st>>>(a, 0);
             }
             e = cudaGetLastError();
@@ -655,14 +655,15 @@ int launch_split(const SlotDesc* slots, const int32_t* arena, uint64_t n, int32_
     return e == cudaSuccess ? GFD_OK : cuda_fail(e, "k_split");
 }
 
-int capture_steps(const EnumArgs& a, int block_threads, int steps, cudaStream_t st, cudaGraph_t* graph,
-                  cudaGraphExec_t* exec) {
-    const int grid = block_threads == 512 ? expand_grid<512>() : expand_grid<256>();
+namespace {
+
+template <int NT, int MINB>
+int capture_steps_t(const EnumArgs& a, int steps, cudaStream_t st, cudaGraph_t* graph, cudaGraphExec_t* exec) {
+    const int grid = expand_grid<NT, MINB>();
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         for (int it = 0; it < steps; it++) {
-            if (block_threads == 512) k_expand<512><<<grid, 512, 0, st>>>(a);
-            else k_expand<256><<<grid, 256, 0, st>>>(a);
+            k_expand<NT, MINB><<<grid, NT, 0, st>>>(a);
             k_control<<<1, CTRL_THREADS, 0, st>>>(a, 0);
         }
         e = cudaStreamEndCapture(st, graph);
@@ -672,22 +673,52 @@ int capture_steps(const EnumArgs& a, int block_threads, int steps, cudaStream_t 
     return GFD_OK;
 }
 
+template <int NT, int MINB>
+int run_variant(const EnumArgs& a, bool persistent, bool use_graph, cudaStream_t st, int64_t* launches) {
+    return persistent ? launch_persistent<NT, MINB>(a, st, launches) : host_loop<NT, MINB>(a, use_graph, st, launches);
+}
+
+}  // namespace
+
+// Kernel variants: threads per block and the minimum resident blocks per SM the
+// compiler must allow (which caps registers per thread).
+int variant_threads(int v) {
+    switch (v) {
+        case 3: case 4: return 128;
+        case 5: return 512;
+        default: return 256;
+    }
+}
+
+int capture_steps(const EnumArgs& a, int variant, int steps, cudaStream_t st, cudaGraph_t* graph,
+                  cudaGraphExec_t* exec) {
+    switch (variant) {
+        case 1: return capture_steps_t<256, 6>(a, steps, st, graph, exec);
+        case 2: return capture_steps_t<256, 8>(a, steps, st, graph, exec);
+        case 3: return capture_steps_t<128, 12>(a, steps, st, graph, exec);
+        case 4: return capture_steps_t<128, 16>(a, steps, st, graph, exec);
+        case 5: return capture_steps_t<512, 3>(a, steps, st, graph, exec);
+        default: return capture_steps_t<256, 4>(a, steps, st, graph, exec);
+    }
+}
+
 int enum_init(const EnumArgs& a, cudaStream_t st) {
     k_control<<<1, CTRL_THREADS, 0, st>>>(a, 1);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GFD_OK : cuda_fail(e, "k_control");
 }
 
-int enum_run(const EnumArgs& a, bool persistent, bool use_graph, int block_threads, cudaStream_t st,
-             cudaEvent_t ev0, cudaEvent_t ev1, int64_t* launches) {
+int enum_run(const EnumArgs& a, bool persistent, bool use_graph, int variant, cudaStream_t st, cudaEvent_t ev0,
+             cudaEvent_t ev1, int64_t* launches) {
     if (ev0) cudaEventRecord(ev0, st);
     int rc;
-    if (persistent) {
-        rc = block_threads == 512 ? launch_persistent<512>(a, st, launches)
-                                  : launch_persistent<256>(a, st, launches);
-    } else {
-        rc = block_threads == 512 ? host_loop<512>(a, use_graph, st, launches)
-                                  : host_loop<256>(a, use_graph, st, launches);
+    switch (variant) {
+        case 1: rc = run_variant<256, 6>(a, persistent, use_graph, st, launches); break;
+        case 2: rc = run_variant<256, 8>(a, persistent, use_graph, st, launches); break;
+        case 3: rc = run_variant<128, 12>(a, persistent, use_graph, st, launches); break;
+        case 4: rc = run_variant<128, 16>(a, persistent, use_graph, st, launches); break;
+        case 5: rc = run_variant<512, 3>(a, persistent, use_graph, st, launches); break;
+        default: rc = run_variant<256, 4>(a, persistent, use_graph, st, launches); break;
     }
     if (ev1) cudaEventRecord(ev1, st);
     return rc;

@@ -577,6 +577,12 @@ int group_launch(gfd_graph* g, Group* G, const Tables& T, cudaStream_t st, ProfE
     return GFD_OK;
 }
 
+// kernel_variant 1..N selects a variant; 0 takes the graph's tuned one.
+int pick_variant(const gfd_graph* g, const gfd_opts* o) {
+    if (o && o->kernel_variant >= 1 && o->kernel_variant <= N_VARIANTS) return o->kernel_variant - 1;
+    return g->tuned_variant >= 0 ? g->tuned_variant : 0;
+}
+
 int64_t default_budget(const gfd_opts* o) {
     if (o && o->frontier_budget_bytes > 0) return o->frontier_budget_bytes;
     size_t fr = 0, tot = 0;
@@ -619,12 +625,15 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
     const bool refine = !(flags & GFD_FLAG_NO_REFINE);
     const bool persistent = !(flags & GFD_FLAG_HOST_LOOP);
     const bool use_graph = !(flags & GFD_FLAG_NO_GRAPH);
-    const int block_threads = (o && o->block_threads == 512) ? 512 : 256;
+    const int variant = pick_variant(g, o);
+    const int block_threads = variant_threads(variant);
     cudaStream_t st = (o && o->cuda_stream) ? (cudaStream_t)o->cuda_stream : g->stream;
     const uint64_t vcap = o && o->max_violations_hint > 0 ? (uint64_t)o->max_violations_hint : (1ull << 22);
 
     Group G;
-    if (int rc = group_plan(g, phis, n, o, default_budget(o) / n, &G)) return rc;
+    const int64_t budget = (!o || o->frontier_budget_bytes <= 0) && g->tuned_budget > 0 ? g->tuned_budget
+                                                                                        : default_budget(o);
+    if (int rc = group_plan(g, phis, n, o, budget / n, &G)) return rc;
     int kmax = 1;
     for (auto& P : G.plans) kmax = std::max(kmax, P.k);
     cudaMemPool_t pool;
@@ -652,7 +661,7 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
     if (int rc = group_launch(g, &G, T, st, prof, launches)) return rc;
     const EnumArgs A = enum_args(g, T);
     if (int rc = enum_init(A, st)) return rc;
-    if (int rc = enum_run(A, persistent, use_graph, block_threads, st, prof.on ? prof.ev[2 * PROF_ENUM] : nullptr,
+    if (int rc = enum_run(A, persistent, use_graph, variant, st, prof.on ? prof.ev[2 * PROF_ENUM] : nullptr,
                           prof.on ? prof.ev[2 * PROF_ENUM + 1] : nullptr, &launches[PROF_ENUM]))
         return rc;
     launches[PROF_ENUM] += 1;
@@ -760,6 +769,7 @@ struct gfd_session {
     cudaStream_t st = nullptr;
     cudaMemPool_t pool = nullptr;
     gfd::Tables T;
+    int variant = 0;
     int block_threads = 256;
     int64_t budget = 0;     // device bytes for the workspaces of running requests
     int64_t used = 0;
@@ -784,7 +794,8 @@ int session_create(gfd_graph* g, int32_t max_slots, const gfd_opts* o, gfd_sessi
     S->g = g;
     if (o) S->opts = *o;
     S->st = o && o->cuda_stream ? (cudaStream_t)o->cuda_stream : g->stream;
-    S->block_threads = (o && o->block_threads == 512) ? 512 : 256;
+    S->variant = pick_variant(g, o);
+    S->block_threads = variant_threads(S->variant);
     S->budget = default_budget(o);
     S->viol_cap = o && o->max_violations_hint > 0 ? (uint64_t)o->max_violations_hint : (1ull << 20);
     S->slots.resize(max_slots);
@@ -793,7 +804,7 @@ int session_create(gfd_graph* g, int32_t max_slots, const gfd_opts* o, gfd_sessi
     if (int rc = mark_idle(S->T.state, max_slots, S->st)) return rc;  // every slot starts idle
     // the enumeration steps of one round, captured once (the tables never move)
     const EnumArgs A = enum_args(g, S->T);
-    if (int rc = capture_steps(A, S->block_threads, S->steps_per_round, S->st, &S->graph, &S->exec)) return rc;
+    if (int rc = capture_steps(A, S->variant, S->steps_per_round, S->st, &S->graph, &S->exec)) return rc;
     GFD_CUDA(cudaStreamSynchronize(S->st));
     *out = S.release();
     return GFD_OK;
@@ -985,6 +996,54 @@ int session_next_result(gfd_session* S, int64_t* id, gfd_result** out) {
     *id = S->done.front().first;
     *out = S->done.front().second;
     S->done.pop_front();
+    return GFD_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+int autotune(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opts* o, gfd_opts* best) {
+    if (!g || (!phis && n > 0) || n <= 0) {
+        set_error(GFD_ERR_INVALID_ARG, "gfd_autotune: empty batch");
+        return GFD_ERR_INVALID_ARG;
+    }
+    const int64_t b0 = default_budget(o);
+    const int64_t budgets[2] = {b0, std::max<int64_t>(b0 / 4, (int64_t)1 << 28)};
+    double best_ms = -1;
+    int best_v = 0;
+    int64_t best_b = b0;
+    std::vector<gfd_result*> res(n, nullptr);
+    for (int bi = 0; bi < 2; bi++)
+        for (int v = 0; v < N_VARIANTS; v++) {
+            gfd_opts t = o ? *o : gfd_opts{};
+            t.kernel_variant = v + 1;
+            t.frontier_budget_bytes = budgets[bi];
+            t.flags |= GFD_FLAG_PROFILE;
+            t.flags &= ~GFD_FLAG_HOST_LOOP;
+            const int rc = run_batch(g, phis, n, &t, res.data());
+            if (rc == GFD_ERR_CUDA || rc == GFD_ERR_OUT_OF_MEMORY) continue;  // variant not usable here
+            if (rc) return rc;
+            double ms = 0;
+            for (int w = 0; w < 4; w++) ms += res[0]->prof_ms[w];
+            for (auto& r : res) {
+                gfd_result_free(r);
+                r = nullptr;
+            }
+            if (best_ms < 0 || ms < best_ms) {
+                best_ms = ms;
+                best_v = v;
+                best_b = budgets[bi];
+            }
+        }
+    if (best_ms < 0) {
+        set_error(GFD_ERR_CUDA, "gfd_autotune: no variant ran");
+        return GFD_ERR_CUDA;
+    }
+    g->tuned_variant = best_v;
+    g->tuned_budget = best_b;
+    if (best) {
+        *best = o ? *o : gfd_opts{};
+        best->kernel_variant = best_v + 1;
+        best->frontier_budget_bytes = best_b;
+    }
     return GFD_OK;
 }
 

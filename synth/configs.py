@@ -163,23 +163,43 @@ def batched(scale: int = 1, n_gfds: int = BATCH_N) -> tuple[Graph, list[GFD]]:
 KG_V, KG_E, KG_N = 20_000_000, 200_000_000, 32
 
 
-def kg_gfds(n: int = KG_N) -> list[GFD]:
+KG_CAP = 1e8
+
+
+def kg_gfds(graph: Graph, n: int = KG_N, n_elabels: int = 64) -> list[GFD]:
     """x-[e]->y, x-[e']->y', y->z1, y'->z1, y->z2, y'->z2, x->w (core
-    {x,y,y',z1,z2}, leaf w). Half are y.A0 = c1 ∧ y'.A0 = c2 → false, the others
-    have one variable Y literal."""
+    {x,y,y',z1,z2}, leaf w). y and y' carry one of the 8 most frequent vertex
+    labels (drawn by frequency), x, z1, z2 such a label or the wildcard with
+    equal odds, w the wildcard; e and e' are a uniform edge label or the
+    wildcard with equal odds, the shared-neighbour edges and x->w the wildcard.
+    Half the GFDs are y.A0 = c1 ∧ y'.A0 = c2 → false (constants drawn from the
+    attribute distribution), the others ∅ → y.A0 = y'.A0. A draw whose expected
+    match count under the configuration model exceeds 1e8 is redrawn."""
+    from .estimate import DegreeMoments
     rng = _rng(3, 1)
+    dm = DegreeMoments(graph, n_elabels)
+    freq = np.bincount(graph.vlabel, minlength=8).astype(np.float64)
+    top = np.argsort(-freq, kind="stable")[:8]
+    p_top = freq[top] / max(1.0, freq[top].sum())
+
+    def lab(p_wild):
+        return -1 if rng.random() < p_wild else int(rng.choice(top, p=p_top))
+
     out = []
     for i in range(n):
-        el = [int(v) for v in rng.integers(0, 8, size=7)]
-        nl = [int(v) for v in rng.integers(0, 8, size=6)]
-        edges = [(0, 1, el[0]), (0, 2, el[1]), (1, 3, el[2]), (2, 3, el[3]),
-                 (1, 4, el[4]), (2, 4, el[5]), (0, 5, el[6])]
-        if i % 2 == 0:
-            c1, c2 = (int(v) for v in zipf_values(2, 1024, 1.1, rng))
-            g = GFD(nl, edges, [Literal.const(1, 0, c1), Literal.const(2, 0, c2)], [],
-                    True, f"kg{i}_false")
-        else:
-            g = GFD(nl, edges, [], [Literal.var(1, 0, 2, 0)], False, f"kg{i}_var")
+        while True:
+            nl = [lab(0.5), lab(0.0), lab(0.0), lab(0.5), lab(0.5), -1]
+            e1 = -1 if rng.random() < 0.5 else int(rng.integers(0, n_elabels))
+            e2 = -1 if rng.random() < 0.5 else int(rng.integers(0, n_elabels))
+            edges = [(0, 1, e1), (0, 2, e2), (1, 3, -1), (2, 3, -1), (1, 4, -1), (2, 4, -1), (0, 5, -1)]
+            if i % 2 == 0:
+                c1, c2 = (int(v) for v in zipf_values(2, 1024, 1.1, rng))
+                g = GFD(nl, edges, [Literal.const(1, 0, c1), Literal.const(2, 0, c2)], [], True,
+                        f"kg{i}_false")
+            else:
+                g = GFD(nl, edges, [], [Literal.var(1, 0, 2, 0)], False, f"kg{i}_var")
+            if dm.expected_count(g) <= KG_CAP:
+                break
         out.append(g)
     return out
 
@@ -190,7 +210,7 @@ def kg(scale: int = 1) -> tuple[Graph, list[GFD]]:
     g = powerlaw_graph(3, n, KG_E // scale, 500, 1.3, 64, 2, 1024, 1.1,
                        gamma_out=2.28, gamma_in=2.5,
                        out_cap_frac=min(1.0, 1e6 / (KG_E // scale)), name="kg")
-    return g, kg_gfds()
+    return g, kg_gfds(g)
 
 
 # ------------------------------------------------------------------------ serving
