@@ -203,3 +203,22 @@ def test_rejects_invalid_inputs(lib):
     bad3.out_dst = np.array([1, 7], np.int32)                          # out of range
     with pytest.raises(G.GfdError):
         gpu_graph(bad3)
+
+
+def test_kernel_variants_and_autotune(lib, oracle_mod):
+    """Every enumeration-kernel variant gives the oracle's answer; the autotuner
+    picks one of them and later default calls still agree."""
+    g, qs = configs.batched(scale=400, n_gfds=16)
+    dg = gpu_graph(g)
+    og = oracle_mod.OracleGraph(g)
+    want = [oracle_mod.validate(og, q) for q in qs]
+    for v in range(1, 7):
+        for flags in (0, G.FLAG_HOST_LOOP):
+            res = dg.validate_batch(qs, kernel_variant=v, flags=flags)
+            for i, r in enumerate(res):
+                assert_same((r.n_matches, r.violations()), want[i], f"variant {v} flags {flags} gfd {i}")
+    best = dg.autotune(qs)
+    assert 1 <= best["kernel_variant"] <= 6 and best["frontier_budget_bytes"] > 0
+    res = dg.validate_batch(qs)
+    for i, r in enumerate(res):
+        assert_same((r.n_matches, r.violations()), want[i], f"tuned gfd {i}")
