@@ -192,6 +192,20 @@ def run_reference(args, g, qs, desc):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ ranks
+def aggregate(step_ms: float, matches: int, dist=None, device: str = "cpu"):
+    """Whole-job figures over the ranks of a replicated run: the step time is
+    the slowest rank's, the throughput all ranks' matches over that time."""
+    import torch
+    t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+    m = torch.tensor([float(matches)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(m, op=dist.ReduceOp.SUM)
+    step_max = float(t.item())
+    return step_max, float(m.item()) / (step_max / 1000.0)
+
+
 # ------------------------------------------------------------------ GPU arm
 def kernel_traffic():
     """dram bytes per launch of the enumeration kernel from the committed ncu
@@ -310,14 +324,7 @@ def main():
     rows = sum(r.stat(G.STAT_ROWS) for r in stats)
     probes = stats[0].stat(G.STAT_PROBES)
     step_ms = float(np.mean(times))
-    # max over ranks
-    t_local = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
-    m_local = torch.tensor([float(matches)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-        dist.all_reduce(m_local, op=dist.ReduceOp.SUM)
-    step_ms_max = float(t_local.item())
-    value = float(m_local.item()) / (step_ms_max / 1000.0)
+    step_ms_max, value = aggregate(step_ms, matches, dist, "cuda")
 
     # algorithmic bytes of one enumeration launch
     lit_bytes = sum(r.n_matches * 32 * literal_attrs(q) for r, q in zip(stats, qs))
