@@ -166,7 +166,7 @@ KG_V, KG_E, KG_N = 20_000_000, 200_000_000, 32
 KG_CAP = 1e8
 
 
-def kg_gfds(graph: Graph, n: int = KG_N, n_elabels: int = 64) -> list[GFD]:
+def kg_gfds(graph: Graph, n: int = KG_N, n_elabels: int = 64, cap: float = KG_CAP) -> list[GFD]:
     """x-[e]->y, x-[e']->y', y->z1, y'->z1, y->z2, y'->z2, x->w (core
     {x,y,y',z1,z2}, leaf w). y and y' carry one of the 8 most frequent vertex
     labels (drawn by frequency), x, z1, z2 such a label or the wildcard with
@@ -174,7 +174,7 @@ def kg_gfds(graph: Graph, n: int = KG_N, n_elabels: int = 64) -> list[GFD]:
     wildcard with equal odds, the shared-neighbour edges and x->w the wildcard.
     Half the GFDs are y.A0 = c1 ∧ y'.A0 = c2 → false (constants drawn from the
     attribute distribution), the others ∅ → y.A0 = y'.A0. A draw whose expected
-    match count under the configuration model exceeds 1e8 is redrawn."""
+    match count under the configuration model exceeds `cap` (1e8) is redrawn."""
     from .estimate import DegreeMoments
     rng = _rng(3, 1)
     dm = DegreeMoments(graph, n_elabels)
@@ -198,7 +198,7 @@ def kg_gfds(graph: Graph, n: int = KG_N, n_elabels: int = 64) -> list[GFD]:
                         f"kg{i}_false")
             else:
                 g = GFD(nl, edges, [], [Literal.var(1, 0, 2, 0)], False, f"kg{i}_var")
-            if dm.expected_count(g) <= KG_CAP:
+            if dm.expected_count(g) <= cap:
                 break
         out.append(g)
     return out
