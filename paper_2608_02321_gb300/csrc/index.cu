@@ -143,6 +143,12 @@ __global__ void __launch_bounds__(COMPACT_THREADS) k_compact_write(DevGraph g, c
     }
 }
 
+// The adjacency kernels below give each lane of a warp one candidate and let
+// the lane scan a short list alone; lists longer than SHORT_LIST are left to
+// the whole warp, one after the other (ballot of the long ones), so hubs are
+// scanned 32 edges at a time without idling lanes on short lists.
+constexpr uint32_t SHORT_LIST = 32;
+
 __global__ void k_scatter(DevGraph g, const ScatterJob* __restrict__ jobs, int njobs) {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
@@ -151,17 +157,60 @@ __global__ void k_scatter(DevGraph g, const ScatterJob* __restrict__ jobs, int n
         const uint32_t n = *J.qcount;
         const uint32_t* off = J.scan_out ? g.out_off : g.in_off;
         const uint32_t* adj = J.scan_out ? g.out_adj : g.in_adj;
-        for (uint64_t a = (gw + (uint64_t)j * 7919) % nw; a < n; a += nw) {
-            const uint32_t v = (uint32_t)J.qcand[a];
-            const uint32_t e1 = off[v + 1];
-            for (uint32_t e = off[v] + lane; e < e1; e += 32) {
-                const uint32_t p = adj[e];
-                const uint32_t x = p >> g.lbits;
-                if (label_ok(J.lab, (int32_t)(p & g.lmask)) && bit_of(J.filter, x))
-                    atomicOr(&J.marks[x >> 5], 1u << (x & 31));
+        const uint64_t groups = (n + 31) / 32;
+        for (uint64_t grp = (gw + (uint64_t)j * 7919) % nw; grp < groups; grp += nw) {
+            const uint64_t a = grp * 32 + lane;
+            uint32_t e0 = 0, e1 = 0;
+            if (a < n) {
+                const uint32_t v = (uint32_t)J.qcand[a];
+                e0 = off[v];
+                e1 = off[v + 1];
+            }
+            const bool is_long = e1 - e0 > SHORT_LIST;
+            if (!is_long)
+                for (uint32_t e = e0; e < e1; e++) {
+                    const uint32_t p = adj[e];
+                    const uint32_t x = p >> g.lbits;
+                    if (label_ok(J.lab, (int32_t)(p & g.lmask)) && bit_of(J.filter, x))
+                        atomicOr(&J.marks[x >> 5], 1u << (x & 31));
+                }
+            for (uint32_t lm = __ballot_sync(0xffffffffu, is_long); lm; lm &= lm - 1) {
+                const int src = __ffs(lm) - 1;
+                const uint32_t b0 = __shfl_sync(0xffffffffu, e0, src), b1 = __shfl_sync(0xffffffffu, e1, src);
+                for (uint32_t e = b0 + lane; e < b1; e += 32) {
+                    const uint32_t p = adj[e];
+                    const uint32_t x = p >> g.lbits;
+                    if (label_ok(J.lab, (int32_t)(p & g.lmask)) && bit_of(J.filter, x))
+                        atomicOr(&J.marks[x >> 5], 1u << (x & 31));
+                }
             }
         }
     }
+}
+
+// Does the list adj[e0, e1) hold a neighbour in bm with an allowed label? One
+// lane alone (short lists) or the whole warp (cooperative).
+__device__ __forceinline__ bool any_hit_serial(const DevGraph& g, const uint32_t* adj, uint32_t e0, uint32_t e1,
+                                               int32_t lab, const uint32_t* bm) {
+    for (uint32_t e = e0; e < e1; e++) {
+        const uint32_t p = adj[e];
+        if (label_ok(lab, (int32_t)(p & g.lmask)) && bit_of(bm, p >> g.lbits)) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool any_hit_warp(const DevGraph& g, const uint32_t* adj, uint32_t e0, uint32_t e1,
+                                             int32_t lab, const uint32_t* bm, int lane) {
+    for (uint32_t b = e0; b < e1; b += 32) {
+        const uint32_t e = b + lane;
+        bool hit = false;
+        if (e < e1) {
+            const uint32_t p = adj[e];
+            hit = label_ok(lab, (int32_t)(p & g.lmask)) && bit_of(bm, p >> g.lbits);
+        }
+        if (__any_sync(0xffffffffu, hit)) return true;
+    }
+    return false;
 }
 
 __global__ void k_prune(DevGraph g, const PruneJob* __restrict__ jobs, int njobs) {
@@ -171,28 +220,30 @@ __global__ void k_prune(DevGraph g, const PruneJob* __restrict__ jobs, int njobs
         const PruneJob& J = jobs[j];
         const uint32_t n = *J.count;
         const int ncon = J.ncon;
-        for (uint64_t a = (gw + (uint64_t)j * 7919) % nw; a < n; a += nw) {
-            const uint32_t v = (uint32_t)J.cand[a];
-            bool keep = true;
-            for (int c = 0; c < ncon && keep; c++) {
+        const uint64_t groups = (n + 31) / 32;
+        for (uint64_t grp = (gw + (uint64_t)j * 7919) % nw; grp < groups; grp += nw) {
+            const uint64_t a = grp * 32 + lane;
+            const bool valid = a < n;
+            const uint32_t v = valid ? (uint32_t)J.cand[a] : 0u;
+            bool keep = valid;
+            for (int c = 0; c < ncon; c++) {
                 const uint32_t* off = J.con_dir[c] ? g.out_off : g.in_off;
                 const uint32_t* adj = J.con_dir[c] ? g.out_adj : g.in_adj;
-                const uint32_t* bm = J.con_bm[c];
-                const int32_t lab = J.con_lab[c];
-                const uint32_t e1 = off[v + 1];
-                bool found = false;
-                for (uint32_t e0 = off[v]; e0 < e1 && !found; e0 += 32) {
-                    const uint32_t e = e0 + lane;
-                    bool hit = false;
-                    if (e < e1) {
-                        const uint32_t p = adj[e];
-                        hit = label_ok(lab, (int32_t)(p & g.lmask)) && bit_of(bm, p >> g.lbits);
-                    }
-                    found = __any_sync(0xffffffffu, hit);
+                uint32_t e0 = 0, e1 = 0;
+                if (keep) {
+                    e0 = off[v];
+                    e1 = off[v + 1];
                 }
-                keep = found;
+                const bool is_long = keep && e1 - e0 > SHORT_LIST;
+                if (keep && !is_long) keep = any_hit_serial(g, adj, e0, e1, J.con_lab[c], J.con_bm[c]);
+                for (uint32_t lm = __ballot_sync(0xffffffffu, is_long); lm; lm &= lm - 1) {
+                    const int src = __ffs(lm) - 1;
+                    const uint32_t b0 = __shfl_sync(0xffffffffu, e0, src), b1 = __shfl_sync(0xffffffffu, e1, src);
+                    const bool hit = any_hit_warp(g, adj, b0, b1, J.con_lab[c], J.con_bm[c], lane);
+                    if (lane == src) keep = hit;
+                }
             }
-            if (!keep && lane == 0) atomicAnd(&J.bm[v >> 5], ~(1u << (v & 31)));
+            if (valid && !keep) atomicAnd(&J.bm[v >> 5], ~(1u << (v & 31)));
         }
     }
 }
@@ -206,16 +257,34 @@ __global__ void k_cpi_count(DevGraph g, const CpiJob* __restrict__ jobs, int njo
         const uint32_t n = *J.pcount;
         const uint32_t* off = J.out ? g.out_off : g.in_off;
         const uint32_t* adj = J.out ? g.out_adj : g.in_adj;
-        for (uint64_t a = (gw + (uint64_t)j * 7919) % nw; a < n; a += nw) {
-            const uint32_t v = (uint32_t)J.pcand[a];
-            const uint32_t e1 = off[v + 1];
-            uint32_t cnt = 0;
-            for (uint32_t e = off[v] + lane; e < e1; e += 32) {
-                const uint32_t p = adj[e];
-                cnt += label_ok(J.lab, (int32_t)(p & g.lmask)) && bit_of(J.cbm, p >> g.lbits);
+        const uint64_t groups = (n + 31) / 32;
+        for (uint64_t grp = (gw + (uint64_t)j * 7919) % nw; grp < groups; grp += nw) {
+            const uint64_t a = grp * 32 + lane;
+            uint32_t e0 = 0, e1 = 0;
+            if (a < n) {
+                const uint32_t v = (uint32_t)J.pcand[a];
+                e0 = off[v];
+                e1 = off[v + 1];
             }
-            cnt = __reduce_add_sync(0xffffffffu, cnt);
-            if (lane == 0) J.off[a] = cnt;
+            const bool is_long = e1 - e0 > SHORT_LIST;
+            uint32_t cnt = 0;
+            if (!is_long)
+                for (uint32_t e = e0; e < e1; e++) {
+                    const uint32_t p = adj[e];
+                    cnt += label_ok(J.lab, (int32_t)(p & g.lmask)) && bit_of(J.cbm, p >> g.lbits);
+                }
+            for (uint32_t lm = __ballot_sync(0xffffffffu, is_long); lm; lm &= lm - 1) {
+                const int src = __ffs(lm) - 1;
+                const uint32_t b0 = __shfl_sync(0xffffffffu, e0, src), b1 = __shfl_sync(0xffffffffu, e1, src);
+                uint32_t c = 0;
+                for (uint32_t e = b0 + lane; e < b1; e += 32) {
+                    const uint32_t p = adj[e];
+                    c += label_ok(J.lab, (int32_t)(p & g.lmask)) && bit_of(J.cbm, p >> g.lbits);
+                }
+                c = __reduce_add_sync(0xffffffffu, c);
+                if (lane == src) cnt = c;
+            }
+            if (a < n) J.off[a] = cnt;
         }
     }
 }
@@ -298,29 +367,54 @@ __global__ void k_cpi_fill(DevGraph g, const CpiJob* __restrict__ jobs, int njob
         const uint32_t n = *J.pcount;
         const uint32_t* off = J.out ? g.out_off : g.in_off;
         const uint32_t* adj = J.out ? g.out_adj : g.in_adj;
-        for (uint64_t a = (gw + (uint64_t)j * 7919) % nw; a < n; a += nw) {
-            const uint32_t v = (uint32_t)J.pcand[a];
-            const uint32_t e1 = off[v + 1];
-            uint32_t o = J.off[a];
-            const uint32_t oend = J.off[a + 1];
-            for (uint32_t e0 = off[v]; e0 < e1; e0 += 32) {
-                const uint32_t e = e0 + lane;
-                bool hit = false;
-                uint32_t x = 0;
-                if (e < e1) {
+        const uint64_t groups = (n + 31) / 32;
+        for (uint64_t grp = (gw + (uint64_t)j * 7919) % nw; grp < groups; grp += nw) {
+            const uint64_t a = grp * 32 + lane;
+            uint32_t e0 = 0, e1 = 0, o = 0, oend = 0;
+            if (a < n) {
+                const uint32_t v = (uint32_t)J.pcand[a];
+                e0 = off[v];
+                e1 = off[v + 1];
+                o = J.off[a];
+                oend = J.off[a + 1];
+            }
+            const bool is_long = e1 - e0 > SHORT_LIST;
+            if (!is_long)
+                for (uint32_t e = e0; e < e1; e++) {
                     const uint32_t p = adj[e];
-                    x = p >> g.lbits;
-                    hit = label_ok(J.lab, (int32_t)(p & g.lmask)) && bit_of(J.cbm, x);
-                }
-                const uint32_t b = __ballot_sync(0xffffffffu, hit);
-                if (hit) {
-                    const uint32_t slot = o + __popc(b & ((1u << lane) - 1));
-                    if (slot < oend && slot < J.cap) {
-                        const uint32_t word = J.cbm[x >> 5];
-                        J.idx[slot] = (int32_t)(J.crank[x >> 5] + __popc(word & ((1u << (x & 31)) - 1)));
+                    const uint32_t x = p >> g.lbits;
+                    if (label_ok(J.lab, (int32_t)(p & g.lmask)) && bit_of(J.cbm, x)) {
+                        if (o < oend && o < J.cap) {
+                            const uint32_t word = J.cbm[x >> 5];
+                            J.idx[o] = (int32_t)(J.crank[x >> 5] + __popc(word & ((1u << (x & 31)) - 1)));
+                        }
+                        o++;
                     }
                 }
-                o += __popc(b);
+            for (uint32_t lm = __ballot_sync(0xffffffffu, is_long); lm; lm &= lm - 1) {
+                const int src = __ffs(lm) - 1;
+                const uint32_t b0 = __shfl_sync(0xffffffffu, e0, src), b1 = __shfl_sync(0xffffffffu, e1, src);
+                uint32_t w = __shfl_sync(0xffffffffu, o, src);
+                const uint32_t wend = __shfl_sync(0xffffffffu, oend, src);
+                for (uint32_t bb = b0; bb < b1; bb += 32) {
+                    const uint32_t e = bb + lane;
+                    bool hit = false;
+                    uint32_t x = 0;
+                    if (e < b1) {
+                        const uint32_t p = adj[e];
+                        x = p >> g.lbits;
+                        hit = label_ok(J.lab, (int32_t)(p & g.lmask)) && bit_of(J.cbm, x);
+                    }
+                    const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+                    if (hit) {
+                        const uint32_t slot = w + __popc(bal & ((1u << lane) - 1));
+                        if (slot < wend && slot < J.cap) {
+                            const uint32_t word = J.cbm[x >> 5];
+                            J.idx[slot] = (int32_t)(J.crank[x >> 5] + __popc(word & ((1u << (x & 31)) - 1)));
+                        }
+                    }
+                    w += __popc(bal);
+                }
             }
         }
     }
