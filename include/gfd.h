@@ -142,6 +142,8 @@ typedef struct {
                                       GFDs of a call together) */
     void *cuda_stream;             /* cudaStream_t to issue work on */
     int32_t flags;                 /* GFD_FLAG_* */
+    int32_t tile_iters;            /* work items per block visit, in units of the
+                                      block size (0: tuned choice or 8) */
 } gfd_opts;
 
 /* Copy a graph to the device, validate it (row order, ranges, label limits,
@@ -151,13 +153,13 @@ int gfd_graph_load(const gfd_graph_desc *desc, const gfd_opts *opts, gfd_graph *
 /* Release a graph handle and its device memory. */
 void gfd_graph_free(gfd_graph *g);
 
-/* Autotuner: validate the batch phis[0..n) once per enumeration-kernel variant
- * and frontier budget (the budget of opts, or the default, and a quarter of
- * it), time the device work of each run with CUDA events, and keep the
- * fastest choice in the graph handle, where later calls with kernel_variant 0
- * and no frontier budget of their own use it. *best (may be NULL) receives
- * opts with the chosen kernel_variant and frontier_budget_bytes. The results
- * of the trial runs are discarded. */
+/* Autotuner: validate the batch phis[0..n) once per enumeration-kernel variant,
+ * tile size (8 or 32 block-sized iterations) and frontier budget (the budget of
+ * opts, or the default, and a quarter of it), time the device work of each run
+ * with CUDA events, and keep the fastest choice in the graph handle, where later
+ * calls with kernel_variant 0, tile_iters 0 and no frontier budget of their own
+ * use it. *best (may be NULL) receives opts with the chosen kernel_variant,
+ * tile_iters and frontier_budget_bytes. The trial runs' results are discarded. */
 int gfd_autotune(gfd_graph *g, const gfd_gfd *const *phis, int32_t n, const gfd_opts *opts,
                  gfd_opts *best);
 

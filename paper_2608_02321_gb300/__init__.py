@@ -64,7 +64,7 @@ class gfd_gfd(C.Structure):
 class gfd_opts(C.Structure):
     _fields_ = [("frontier_budget_bytes", C.c_int64), ("chunk_rows", C.c_int32),
                 ("kernel_variant", C.c_int32), ("max_violations_hint", C.c_int64),
-                ("cuda_stream", C.c_void_p), ("flags", C.c_int32)]
+                ("cuda_stream", C.c_void_p), ("flags", C.c_int32), ("tile_iters", C.c_int32)]
 
 
 # exported functions: name -> (restype, argtypes)
@@ -150,7 +150,7 @@ def _stream_handle(stream):
 
 
 def make_opts(frontier_budget_bytes=0, chunk_rows=0, kernel_variant=0, max_violations_hint=0,
-              stream=None, flags=0) -> gfd_opts:
+              stream=None, flags=0, tile_iters=0) -> gfd_opts:
     o = gfd_opts()
     o.frontier_budget_bytes = int(frontier_budget_bytes)
     o.chunk_rows = int(chunk_rows)
@@ -158,6 +158,7 @@ def make_opts(frontier_budget_bytes=0, chunk_rows=0, kernel_variant=0, max_viola
     o.max_violations_hint = int(max_violations_hint)
     o.cuda_stream = _stream_handle(stream)
     o.flags = int(flags)
+    o.tile_iters = int(tile_iters)
     return o
 
 
@@ -289,7 +290,7 @@ class Graph:
         arr = (C.POINTER(gfd_gfd) * max(1, len(bufs)))(*[C.pointer(b.s) for b in bufs])
         best = gfd_opts()
         _check(_lib.gfd_autotune(self._h, arr, len(bufs), C.byref(o), C.byref(best)))
-        return {"kernel_variant": int(best.kernel_variant),
+        return {"kernel_variant": int(best.kernel_variant), "tile_iters": int(best.tile_iters),
                 "frontier_budget_bytes": int(best.frontier_budget_bytes)}
 
     def validate_batch(self, gfds, **opts) -> list:

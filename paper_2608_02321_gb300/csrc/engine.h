@@ -38,6 +38,7 @@ struct gfd_graph {
     std::mutex mu;
     int32_t tuned_variant = -1;          // set by gfd_autotune
     int64_t tuned_budget = 0;
+    int32_t tuned_tile_iters = 0;
 };
 
 struct gfd_result {

@@ -142,8 +142,8 @@ struct Tables {
 
 namespace {
 
-int tables_alloc(cudaMemPool_t pool, int max_slots, int block_threads, int kmax_arena, uint64_t vcap,
-                 bool bounded_run, cudaStream_t st, Tables* T) {
+int tables_alloc(cudaMemPool_t pool, int max_slots, int block_threads, int tile_iters, int kmax_arena,
+                 uint64_t vcap, bool bounded_run, cudaStream_t st, Tables* T) {
     Layout L;
     const size_t o_desc = L.take(sizeof(SlotDesc) * max_slots);
     const size_t o_state = L.take(sizeof(SlotState) * max_slots);
@@ -169,7 +169,7 @@ int tables_alloc(cudaMemPool_t pool, int max_slots, int block_threads, int kmax_
     T->varena = kmax_arena > 0 ? (int32_t*)(T->base + o_arena) : nullptr;
     T->vcap = kmax_arena > 0 ? vcap : 0;
     T->vstride = vstride;
-    T->tile = block_threads * 8;
+    T->tile = block_threads * tile_iters;
     GFD_CUDA(cudaMemsetAsync(T->base + o_desc, 0, zero_end - o_desc, st));
     Sched s{};
     s.n_slots = max_slots;
@@ -583,6 +583,12 @@ int pick_variant(const gfd_graph* g, const gfd_opts* o) {
     return g->tuned_variant >= 0 ? g->tuned_variant : 0;
 }
 
+// work items per block visit in units of the block size (1..64)
+int pick_tile_iters(const gfd_graph* g, const gfd_opts* o) {
+    if (o && o->tile_iters >= 1) return std::min(o->tile_iters, 64);
+    return g->tuned_tile_iters > 0 ? g->tuned_tile_iters : 8;
+}
+
 int64_t default_budget(const gfd_opts* o) {
     if (o && o->frontier_budget_bytes > 0) return o->frontier_budget_bytes;
     size_t fr = 0, tot = 0;
@@ -639,7 +645,7 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
     cudaMemPool_t pool;
     if (int rc = get_pool(g, &pool)) return rc;
     Tables T;
-    if (int rc = tables_alloc(pool, n, block_threads, kmax, vcap, true, st, &T)) return rc;
+    if (int rc = tables_alloc(pool, n, block_threads, pick_tile_iters(g, o), kmax, vcap, true, st, &T)) return rc;
     struct Free {
         std::vector<void*> p;
         cudaStream_t st;
@@ -800,7 +806,8 @@ int session_create(gfd_graph* g, int32_t max_slots, const gfd_opts* o, gfd_sessi
     S->viol_cap = o && o->max_violations_hint > 0 ? (uint64_t)o->max_violations_hint : (1ull << 20);
     S->slots.resize(max_slots);
     if (int rc = get_pool(g, &S->pool)) return rc;
-    if (int rc = tables_alloc(S->pool, max_slots, S->block_threads, 0, 0, false, S->st, &S->T)) return rc;
+    if (int rc = tables_alloc(S->pool, max_slots, S->block_threads, pick_tile_iters(g, o), 0, 0, false, S->st, &S->T))
+        return rc;
     if (int rc = mark_idle(S->T.state, max_slots, S->st)) return rc;  // every slot starts idle
     // the enumeration steps of one round, captured once (the tables never move)
     const EnumArgs A = enum_args(g, S->T);
@@ -1007,14 +1014,17 @@ int autotune(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opts
     }
     const int64_t b0 = default_budget(o);
     const int64_t budgets[2] = {b0, std::max<int64_t>(b0 / 4, (int64_t)1 << 28)};
+    const int tiles[2] = {8, 32};
     double best_ms = -1;
-    int best_v = 0;
+    int best_v = 0, best_t = 8;
     int64_t best_b = b0;
     std::vector<gfd_result*> res(n, nullptr);
     for (int bi = 0; bi < 2; bi++)
+        for (int ti = 0; ti < 2; ti++)
         for (int v = 0; v < N_VARIANTS; v++) {
             gfd_opts t = o ? *o : gfd_opts{};
             t.kernel_variant = v + 1;
+            t.tile_iters = tiles[ti];
             t.frontier_budget_bytes = budgets[bi];
             t.flags |= GFD_FLAG_PROFILE;
             t.flags &= ~GFD_FLAG_HOST_LOOP;
@@ -1030,6 +1040,7 @@ int autotune(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opts
             if (best_ms < 0 || ms < best_ms) {
                 best_ms = ms;
                 best_v = v;
+                best_t = tiles[ti];
                 best_b = budgets[bi];
             }
         }
@@ -1038,10 +1049,12 @@ int autotune(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opts
         return GFD_ERR_CUDA;
     }
     g->tuned_variant = best_v;
+    g->tuned_tile_iters = best_t;
     g->tuned_budget = best_b;
     if (best) {
         *best = o ? *o : gfd_opts{};
         best->kernel_variant = best_v + 1;
+        best->tile_iters = best_t;
         best->frontier_budget_bytes = best_b;
     }
     return GFD_OK;

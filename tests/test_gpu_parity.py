@@ -214,7 +214,7 @@ def test_kernel_variants_and_autotune(lib, oracle_mod):
     want = [oracle_mod.validate(og, q) for q in qs]
     for v in range(1, 7):
         for flags in (0, G.FLAG_HOST_LOOP):
-            res = dg.validate_batch(qs, kernel_variant=v, flags=flags)
+            res = dg.validate_batch(qs, kernel_variant=v, flags=flags, tile_iters=1 + 31 * (v % 2))
             for i, r in enumerate(res):
                 assert_same((r.n_matches, r.violations()), want[i], f"variant {v} flags {flags} gfd {i}")
     best = dg.autotune(qs)
