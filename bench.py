@@ -246,6 +246,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--n-gfds", type=int, default=0, help="validate only the first N GFDs (profiling)")
     ap.add_argument("--no-autotune", action="store_true", help="skip gfd_autotune before the warm-up")
+    ap.add_argument("--kernel-variant", type=int, default=0, help="fixed enumeration kernel variant (1-6)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -286,10 +287,10 @@ def main():
 
     def step():
         return dg.validate_batch(qs, stream=stream, flags=flags, max_violations_hint=hint,
-                                 frontier_budget_bytes=budget)
+                                 frontier_budget_bytes=budget, kernel_variant=args.kernel_variant)
 
     tuned = None
-    if not args.no_autotune:
+    if not args.no_autotune and not args.kernel_variant:
         # untimed: pick the enumeration-kernel variant and frontier budget
         tuned = dg.autotune(qs, stream=stream, max_violations_hint=hint,
                             frontier_budget_bytes=budget)
