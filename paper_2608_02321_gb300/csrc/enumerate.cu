@@ -107,6 +107,14 @@ __device__ __forceinline__ uint32_t find_row(const uint64_t* S, uint64_t n, uint
     return (uint32_t)lo;
 }
 
+// Loads for the searches: index offsets are read-only during the enumeration
+// (read-only cache); frontier prefixes and the per-step tile prefix are
+// rewritten between steps (L2 only).
+__device__ __forceinline__ uint32_t ld_front(const uint32_t* p) { return __ldcg(p); }
+__device__ __forceinline__ uint64_t ld_front(const uint64_t* p) {
+    return __ldcg((const unsigned long long*)p);
+}
+
 // r in [lo, hi) with S[r] <= w < S[r+1]: the search limited to the rows of a tile.
 __device__ __forceinline__ uint32_t find_row_in(const uint32_t* S, uint32_t lo, uint32_t hi, uint64_t w) {
     while (hi - lo > 1) {
@@ -131,34 +139,49 @@ __device__ __forceinline__ int32_t cand_rank(const uint32_t* bm, const uint32_t*
     return (int32_t)(__ldg(rank + (v >> 5)) + __popc(__ldg(bm + (v >> 5)) & ((1u << (v & 31)) - 1u)));
 }
 
-template <int NT>
-__device__ void expand_tiles(const EnumArgs& A) {
-    using Scan = cub::BlockScan<uint64_t, NT>;
-    using Reduce = cub::BlockReduce<uint64_t, NT>;
-    __shared__ union {
-        typename Scan::TempStorage scan;
-        typename Reduce::TempStorage reduce;
-    } tmp;
-    __shared__ uint64_t sh_base2[2];  // double-buffered: no barrier needed after its readers
-    __shared__ int32_t sh_slot;
-    __shared__ uint32_t sh_rlo, sh_rhi;
-    uint32_t parity = 0;
+// Warp-parallel search: largest r in [lo, hi) with S[r] <= w, given S[lo] <= w.
+// Each round probes 32 evenly spaced entries and keeps the last one <= w.
+template <typename T>
+__device__ __forceinline__ uint32_t warp_find(const T* S, uint64_t lo, uint64_t hi, uint64_t w, int lane) {
+    while (hi - lo > 32) {
+        const uint64_t step = (hi - lo + 31) / 32;
+        const uint64_t idx = lo + (uint64_t)lane * step;
+        const bool le = idx < hi && (uint64_t)ld_front(S + idx) <= w;
+        const uint32_t b = __ballot_sync(0xffffffffu, le);
+        const int j = 31 - __clz(b);
+        lo = lo + (uint64_t)j * step;
+        hi = min(hi, lo + step);
+    }
+    const uint64_t idx = lo + lane;
+    const bool le = idx < hi && (uint64_t)ld_front(S + idx) <= w;
+    const uint32_t b = __ballot_sync(0xffffffffu, le);
+    return (uint32_t)(lo + 31 - __clz(b));
+}
+
+// Exclusive warp scan of 64-bit values; *total receives the warp's sum.
+__device__ __forceinline__ uint64_t warp_excl_scan(uint64_t x, int lane, uint64_t* total) {
+    uint64_t incl = x;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    *total = __shfl_sync(0xffffffffu, incl, 31);
+    return incl - x;
+}
+
+// The expansion step, warp-synchronous: every warp takes its own tiles of
+// work items (no block-wide barrier in the loop). A tile belongs to one slot
+// and one level; the warp finds them (and the rows the tile covers) with
+// lane-parallel searches, then processes 32 work items per iteration.
+__device__ void expand_warps(const EnumArgs& A) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t gwarp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const DevGraph& g = A.g;
     const uint32_t total_tiles = *(volatile uint32_t*)&A.sched->total_tiles;
     uint64_t probes = 0;
-    for (uint32_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-        if (threadIdx.x == 0) {
-            // slot of tile t: largest s with tile_base[s] <= t
-            int lo = 0, hi = A.n_slots;
-            while (hi - lo > 1) {
-                int mid = (lo + hi) >> 1;
-                if (__ldcg(A.tile_base + mid) <= t) lo = mid;
-                else hi = mid;
-            }
-            sh_slot = lo;
-        }
-        __syncthreads();
-        const int s = sh_slot;
+    for (uint64_t t = gwarp; t < total_tiles; t += nwarps) {
+        const int s = (int)warp_find(A.tile_base, 0, (uint64_t)A.n_slots, t, lane);
         const SlotDesc* __restrict__ D = A.slots + s;
         SlotState* S = A.state + s;
         const int k = D->k;
@@ -166,33 +189,28 @@ __device__ void expand_tiles(const EnumArgs& A) {
         const int l = __ldcg(&S->cur);
         const int i = k == 1 ? 0 : l + 1;  // level being matched
         const bool last = i == k - 1;
-        const uint64_t wb = __ldcg((const unsigned long long*)&S->cb) +
-                            (uint64_t)(t - __ldcg(A.tile_base + s)) * A.tile;
+        const uint64_t wb = __ldcg((const unsigned long long*)&S->cb) + (t - __ldcg(A.tile_base + s)) * A.tile;
         const uint64_t we = min(wb + (uint64_t)A.tile, (uint64_t)__ldcg((const unsigned long long*)&S->ce));
         const LevelPlan& LP = D->lv[i];
-        // row source
         const uint32_t* S0 = i > 0 ? D->cpi_off[i] : nullptr;
         const uint64_t* Sl = l >= 1 ? D->wpre[l] : nullptr;
         const int32_t* rows_l = l >= 1 ? D->rows[l] : nullptr;
         const uint64_t nrows = k == 1 ? 0 : (l == 0 ? (uint64_t)S->ncand[0]
                                                     : (uint64_t)__ldcg((const unsigned long long*)&S->nrows[l]));
         const int rw = 2 * (l + 1) + 1;  // row width at level l: ids, positions, generator choice
-        if (threadIdx.x == 0 && k > 1) {
-            // the rows this tile's work items belong to
+        uint32_t rlo = 0, rhi1 = 0;
+        if (k > 1) {
             if (l == 0) {
-                sh_rlo = find_row(S0, nrows, wb);
-                sh_rhi = find_row(S0, nrows, we - 1);
+                rlo = warp_find(S0, 0, nrows, wb, lane);
+                rhi1 = warp_find(S0, rlo, nrows, we - 1, lane) + 1;
             } else {
-                sh_rlo = find_row(Sl, nrows, wb);
-                sh_rhi = find_row(Sl, nrows, we - 1);
+                rlo = warp_find(Sl, 0, nrows, wb, lane);
+                rhi1 = warp_find(Sl, rlo, nrows, we - 1, lane) + 1;
             }
         }
-        __syncthreads();
-        const uint32_t rlo = sh_rlo, rhi1 = sh_rhi + 1;
-        for (uint64_t w0 = wb; w0 < we; w0 += NT) {
-            uint64_t& sh_base = sh_base2[parity];
-            parity ^= 1u;
-            const uint64_t w = w0 + threadIdx.x;
+        uint64_t tile_matches = 0;
+        for (uint64_t w0 = wb; w0 < we; w0 += 32) {
+            const uint64_t w = w0 + lane;
             bool ok = w < we;
             uint32_t m[MAXK];
             uint32_t v = 0;
@@ -272,6 +290,7 @@ __device__ void expand_tiles(const EnumArgs& A) {
                 // complete match: count it, check X -> Y, emit a violation
                 bool viol = false;
                 if (ok) {
+                    tile_matches++;
                     bool x_ok = true;
                     for (int q = 0; q < D->nx && x_ok; q++) x_ok = lit_holds(g, D->lit[q], m);
                     if (x_ok) {
@@ -280,32 +299,29 @@ __device__ void expand_tiles(const EnumArgs& A) {
                         viol = !y_ok;
                     }
                 }
-                const uint64_t packed = ((uint64_t)ok << 32) | (uint64_t)viol;
-                uint64_t excl, total;
-                Scan(tmp.scan).ExclusiveSum(packed, excl, total);
-                if (threadIdx.x == 0) {
-                    if (total >> 32) atomicAdd((unsigned long long*)&S->n_matches, (unsigned long long)(total >> 32));
-                    const unsigned long long nv = total & 0xffffffffu;
-                    sh_base = 0;
-                    if (nv) {
+                const uint32_t vb = __ballot_sync(0xffffffffu, viol);
+                if (vb) {
+                    unsigned long long base = 0;
+                    if (lane == 0) {
+                        const unsigned long long nv = __popc(vb);
                         const unsigned long long old = atomicAdd((unsigned long long*)&S->n_viol, nv);
-                        sh_base = D->viol ? old : atomicAdd((unsigned long long*)&A.sched->varena_used, nv);
+                        base = D->viol ? old : atomicAdd((unsigned long long*)&A.sched->varena_used, nv);
                     }
-                }
-                __syncthreads();
-                if (viol) {
-                    const uint64_t idx = sh_base + (excl & 0xffffffffu);
-                    if (D->viol) {
-                        // the slot's own buffer: tuples in pattern-node order
-                        if (idx < D->viol_cap) {
-                            int32_t* out = D->viol + idx * k;
-                            for (int q = 0; q < k; q++) out[D->order[q]] = (int32_t)m[q];
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (viol) {
+                        const uint64_t idx = base + __popc(vb & ((1u << lane) - 1u));
+                        if (D->viol) {
+                            // the slot's own buffer: tuples in pattern-node order
+                            if (idx < D->viol_cap) {
+                                int32_t* out = D->viol + idx * k;
+                                for (int q = 0; q < k; q++) out[D->order[q]] = (int32_t)m[q];
+                            }
+                        } else if (idx < A.sched->varena_cap) {
+                            // the run's arena: [slot, tuple in pattern-node order]
+                            int32_t* rec = A.sched->varena + idx * A.sched->vstride;
+                            rec[0] = s;
+                            for (int q = 0; q < k; q++) rec[1 + D->order[q]] = (int32_t)m[q];
                         }
-                    } else if (idx < A.sched->varena_cap) {
-                        // the run's arena: [slot, tuple in pattern-node order]
-                        int32_t* rec = A.sched->varena + idx * A.sched->vstride;
-                        rec[0] = s;
-                        for (int q = 0; q < k; q++) rec[1 + D->order[q]] = (int32_t)m[q];
                     }
                 }
             } else {
@@ -331,42 +347,44 @@ __device__ void expand_tiles(const EnumArgs& A) {
                     }
                 }
                 const uint64_t packed = ok ? ((1ull << ROW_SHIFT) | fo) : 0ull;
-                uint64_t excl, total;
-                Scan(tmp.scan).ExclusiveSum(packed, excl, total);
-                if (threadIdx.x == 0) {
-                    uint64_t old = 0;
-                    if (total) {
+                uint64_t total;
+                const uint64_t excl = warp_excl_scan(packed, lane, &total);
+                if (total) {
+                    unsigned long long old = 0;
+                    if (lane == 0) {
                         old = atomicAdd((unsigned long long*)&S->ctr[i], (unsigned long long)total);
                         if ((old & WORK_MASK) + (total & WORK_MASK) > WORK_MASK ||
                             (old >> ROW_SHIFT) + (total >> ROW_SHIFT) > D->chunk)
                             atomicExch(&S->err, DERR_COUNTER_OVERFLOW);
                     }
-                    sh_base = old;
-                }
-                __syncthreads();
-                if (ok) {
-                    const uint64_t row = (sh_base >> ROW_SHIFT) + (excl >> ROW_SHIFT);
-                    if (row < D->chunk) {
-                        const int nw = 2 * (i + 1) + 1;
-                        int32_t* dst = D->rows[i] + row * nw;
-                        for (int q = 0; q <= i; q++) dst[q] = (int32_t)m[q];
-                        if (l == 0) {
-                            dst[i + 1] = (int32_t)r;
-                        } else {
-                            for (int q = 0; q <= l; q++) dst[i + 1 + q] = __ldcg(rowp + l + 1 + q);
+                    old = __shfl_sync(0xffffffffu, old, 0);
+                    if (ok) {
+                        const uint64_t row = (old >> ROW_SHIFT) + (excl >> ROW_SHIFT);
+                        if (row < D->chunk) {
+                            const int nw = 2 * (i + 1) + 1;
+                            int32_t* dst = D->rows[i] + row * nw;
+                            for (int q = 0; q <= i; q++) dst[q] = (int32_t)m[q];
+                            if (l == 0) {
+                                dst[i + 1] = (int32_t)r;
+                            } else {
+                                for (int q = 0; q <= l; q++) dst[i + 1 + q] = __ldcg(rowp + l + 1 + q);
+                            }
+                            dst[i + 1 + i] = j;
+                            dst[2 * (i + 1)] = gen;
+                            D->wpre[i][row] = (old & WORK_MASK) + (excl & WORK_MASK);
                         }
-                        dst[i + 1 + i] = j;
-                        dst[2 * (i + 1)] = gen;
-                        D->wpre[i][row] = (sh_base & WORK_MASK) + (excl & WORK_MASK);
                     }
                 }
             }
         }
-        __syncthreads();
+        if (last) {
+            const unsigned long long tm = __reduce_add_sync(0xffffffffu, (unsigned)tile_matches);
+            if (lane == 0 && tm) atomicAdd((unsigned long long*)&S->n_matches, tm);
+        }
     }
-    // probe statistics: one atomic per block
-    const uint64_t p = Reduce(tmp.reduce).Sum(probes);
-    if (threadIdx.x == 0 && p) atomicAdd((unsigned long long*)&A.sched->probes, (unsigned long long)p);
+    // probe statistics: one atomic per warp
+    const unsigned long long p = __reduce_add_sync(0xffffffffu, (unsigned)min(probes, (uint64_t)0xffffffffu));
+    if (lane == 0 && p) atomicAdd((unsigned long long*)&A.sched->probes, p);
 }
 
 // Start the enumeration of a slot whose index is built: level 0 holds the root
@@ -461,7 +479,7 @@ __global__ void __launch_bounds__(CTRL_THREADS) k_control(EnumArgs A, int first)
 
 template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_expand(EnumArgs A) {
-    expand_tiles<NT>(A);
+    expand_warps(A);
 }
 
 // Bounded grid barrier (cooperative launch guarantees co-residency): the last
@@ -505,7 +523,7 @@ __device__ bool grid_barrier(Sched* s) {
 template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_persistent(EnumArgs A) {
     for (;;) {
-        expand_tiles<NT>(A);
+        expand_warps(A);
         if (!grid_barrier(A.sched)) return;
         if (blockIdx.x == 0) control_step<NT>(A, false);
         if (!grid_barrier(A.sched)) return;

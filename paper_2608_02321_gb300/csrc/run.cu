@@ -169,7 +169,7 @@ int tables_alloc(cudaMemPool_t pool, int max_slots, int block_threads, int tile_
     T->varena = kmax_arena > 0 ? (int32_t*)(T->base + o_arena) : nullptr;
     T->vcap = kmax_arena > 0 ? vcap : 0;
     T->vstride = vstride;
-    T->tile = block_threads * tile_iters;
+    T->tile = 32 * tile_iters;  // work items per warp visit
     GFD_CUDA(cudaMemsetAsync(T->base + o_desc, 0, zero_end - o_desc, st));
     Sched s{};
     s.n_slots = max_slots;
