@@ -9,11 +9,12 @@
 //            popcount prefix [nwords] u32 (so rank(v) is O(1)), the sorted
 //            candidate list i32, and for every level i >= 1 the index edges of
 //            the spanning-tree edge (parent(i), i): off u32 [|C(parent)|+1],
-//            idx i32 [nnz] = positions in C(i).
+//            idx int2 [nnz] = (position in C(i), vertex id).
 //   frontier: per (GFD, level l >= 1) a buffer of partial matches, row-major
-//            [chunk][2(l+1)+1] i32 = l+1 vertex ids, l+1 candidate positions and
-//            the generator chosen for level l+1, plus the exclusive prefix of
-//            each row's fan-out u64 [chunk].
+//            [chunk][2(l+1)+2] i32 = l+1 vertex ids, l+1 candidate positions, the
+//            generator chosen for level l+1 and the start of the parent's index
+//            edges for level l+1, plus the exclusive prefix of each row's fan-out
+//            u64 [chunk]. Rows with no fan-out are not stored.
 #pragma once
 
 #include <cstdint>
@@ -96,7 +97,7 @@ struct SlotDesc {
     int32_t* cand[MAXK];
     uint32_t cand_cap[MAXK];
     uint32_t* cpi_off[MAXK];  // level i >= 1
-    int32_t* cpi_idx[MAXK];
+    int2* cpi_idx[MAXK];      // (position in C(i), vertex id) per index edge
     uint64_t cpi_cap[MAXK];
     // frontier
     int32_t* rows[MAXK];      // level l >= 1

@@ -93,7 +93,7 @@ struct CpiJob {          // index edges of one spanning-tree edge
     const uint32_t* cbm;
     const uint32_t* crank;
     uint32_t* off;
-    int32_t* idx;
+    int2* idx;               // (position in C(child), vertex id)
     uint64_t cap;
     int32_t out;             // 1: children are out-neighbours of the parent candidates
     int32_t lab;

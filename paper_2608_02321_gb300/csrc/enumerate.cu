@@ -197,7 +197,7 @@ __device__ void expand_warps(const EnumArgs& A) {
         const int32_t* rows_l = l >= 1 ? D->rows[l] : nullptr;
         const uint64_t nrows = k == 1 ? 0 : (l == 0 ? (uint64_t)S->ncand[0]
                                                     : (uint64_t)__ldcg((const unsigned long long*)&S->nrows[l]));
-        const int rw = 2 * (l + 1) + 1;  // row width at level l: ids, positions, generator choice
+        const int rw = 2 * (l + 1) + 2;  // row width at level l: ids, positions, generator, index base
         uint32_t rlo = 0, rhi1 = 0;
         if (k > 1) {
             if (l == 0) {
@@ -209,6 +209,7 @@ __device__ void expand_warps(const EnumArgs& A) {
             }
         }
         uint64_t tile_matches = 0;
+        uint32_t cur = rlo;  // row of the first work item of the iteration
         for (uint64_t w0 = wb; w0 < we; w0 += 32) {
             const uint64_t w = w0 + lane;
             bool ok = w < we;
@@ -217,33 +218,55 @@ __device__ void expand_warps(const EnumArgs& A) {
             int32_t j = 0;
             const int32_t* rowp = nullptr;
             uint32_t r = 0;
+            // Rows of this iteration's 32 work items: stored rows have fan-out
+            // >= 1, so they lie in the window [cur, cur + 32); one coalesced load
+            // of the window's prefixes and a 5-step shuffle search per lane. A
+            // lane left at the window's end checks the next prefix and falls
+            // back to a binary search (root candidates may have no fan-out).
+            uint64_t sr = 0;
+            if (k > 1) {
+                const uint64_t widx = (uint64_t)cur + lane;
+                const uint64_t sv = widx < rhi1 ? (l == 0 ? (uint64_t)__ldg(S0 + widx) : ld_front(Sl + widx))
+                                                : ~0ull;
+                int pos = 0;
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const uint64_t x = __shfl_sync(0xffffffffu, sv, pos + step);
+                    if (x <= w) pos += step;
+                }
+                sr = __shfl_sync(0xffffffffu, sv, pos);
+                r = cur + pos;
+                if (ok && pos == 31 && r + 1 < rhi1) {
+                    const uint64_t nxt = l == 0 ? (uint64_t)__ldg(S0 + r + 1) : ld_front(Sl + r + 1);
+                    if (nxt <= w) {
+                        r = l == 0 ? find_row_in(S0, r, rhi1, w) : find_row_in(Sl, r, rhi1, w);
+                        sr = l == 0 ? (uint64_t)__ldg(S0 + r) : ld_front(Sl + r);
+                    }
+                }
+                cur = __shfl_sync(0xffffffffu, r, 31);
+            }
             if (ok) {
                 if (k == 1) {
                     j = (int32_t)w;
                     v = (uint32_t)D->cand[0][j];
                 } else {
-                    uint64_t o;
-                    uint32_t pp;
+                    const uint64_t o = w - sr;
+                    uint64_t ent;  // index of the candidate's index edge
                     int choice = 0;
                     if (l == 0) {
-                        r = find_row_in(S0, rlo, rhi1, w);
-                        o = w - __ldg(S0 + r);
-                        pp = r;
+                        ent = w;  // the roots' index edges are level 1's, in work-item order
                         m[0] = (uint32_t)D->cand[0][r];
                     } else {
-                        r = find_row_in(Sl, rlo, rhi1, w);
-                        o = w - __ldcg((const unsigned long long*)Sl + r);
                         rowp = rows_l + (uint64_t)r * rw;
                         for (int q = 0; q <= l; q++) m[q] = (uint32_t)__ldcg(rowp + q);
-                        pp = (uint32_t)__ldcg(rowp + l + 1 + LP.par);
                         choice = __ldcg(rowp + 2 * (l + 1));
+                        ent = (uint64_t)(uint32_t)__ldcg(rowp + 2 * (l + 1) + 1) + o;
                     }
                     int skip = -1;
                     if (choice == 0) {
                         // candidates from the index edges of the spanning-tree parent
-                        const uint32_t base = __ldg(D->cpi_off[i] + pp);
-                        j = __ldg(D->cpi_idx[i] + base + o);
-                        v = (uint32_t)__ldg(D->cand[i] + j);
+                        const int2 e = __ldg(D->cpi_idx[i] + ent);
+                        j = e.x;
+                        v = (uint32_t)e.y;
                     } else {
                         // candidates from the adjacency of the other end of a
                         // required back edge (the shorter list): keep those in
@@ -326,15 +349,18 @@ __device__ void expand_warps(const EnumArgs& A) {
                 }
             } else {
                 // partial match of level i: append it with its fan-out for level
-                // i+1, taken from the shortest candidate generator
+                // i+1, taken from the shortest candidate generator (dead ends,
+                // with no fan-out, are dropped)
                 uint64_t fo = 0;
+                uint32_t nbase = 0;
                 int gen = 0;
                 if (ok) {
                     const LevelPlan& L2 = D->lv[i + 1];
                     const int pn = L2.par;
                     const uint32_t ppn = pn == i ? (uint32_t)j : (l == 0 ? r : (uint32_t)__ldcg(rowp + l + 1 + pn));
                     const uint32_t* co = D->cpi_off[i + 1];
-                    fo = __ldg(co + ppn + 1) - __ldg(co + ppn);
+                    nbase = __ldg(co + ppn);
+                    fo = __ldg(co + ppn + 1) - nbase;
                     for (int q = 0; q < L2.ngen; q++) {
                         const int cg = L2.gen[q];
                         const uint32_t x = m[L2.chk_q[cg]];
@@ -346,6 +372,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                         }
                     }
                 }
+                ok = ok && fo > 0;
                 const uint64_t packed = ok ? ((1ull << ROW_SHIFT) | fo) : 0ull;
                 uint64_t total;
                 const uint64_t excl = warp_excl_scan(packed, lane, &total);
@@ -371,6 +398,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                             }
                             dst[i + 1 + i] = j;
                             dst[2 * (i + 1)] = gen;
+                            dst[2 * (i + 1) + 1] = (int32_t)nbase;
                             D->wpre[i][row] = (old & WORK_MASK) + (excl & WORK_MASK);
                         }
                     }

@@ -386,7 +386,8 @@ __global__ void k_cpi_fill(DevGraph g, const CpiJob* __restrict__ jobs, int njob
                     if (label_ok(J.lab, (int32_t)(p & g.lmask)) && bit_of(J.cbm, x)) {
                         if (o < oend && o < J.cap) {
                             const uint32_t word = J.cbm[x >> 5];
-                            J.idx[o] = (int32_t)(J.crank[x >> 5] + __popc(word & ((1u << (x & 31)) - 1)));
+                            J.idx[o] = make_int2((int32_t)(J.crank[x >> 5] + __popc(word & ((1u << (x & 31)) - 1))),
+                                                 (int32_t)x);
                         }
                         o++;
                     }
@@ -410,7 +411,8 @@ __global__ void k_cpi_fill(DevGraph g, const CpiJob* __restrict__ jobs, int njob
                         const uint32_t slot = w + __popc(bal & ((1u << lane) - 1));
                         if (slot < wend && slot < J.cap) {
                             const uint32_t word = J.cbm[x >> 5];
-                            J.idx[slot] = (int32_t)(J.crank[x >> 5] + __popc(word & ((1u << (x & 31)) - 1)));
+                            J.idx[slot] = make_int2((int32_t)(J.crank[x >> 5] + __popc(word & ((1u << (x & 31)) - 1))),
+                                                    (int32_t)x);
                         }
                     }
                     w += __popc(bal);

@@ -297,7 +297,7 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
         }
         for (size_t q = 0; q < P.lits.size(); q++) D.lit[q] = P.lits[q];
         uint64_t row_bytes = 0;
-        for (int l = 1; l <= P.k - 2; l++) row_bytes += 4ull * (2 * (l + 1) + 1) + 8;
+        for (int l = 1; l <= P.k - 2; l++) row_bytes += 4ull * (2 * (l + 1) + 2) + 8;
         uint64_t chunk = o && o->chunk_rows > 0 ? (uint64_t)o->chunk_rows
                                                 : (row_bytes ? (uint64_t)frontier_per_slot / row_bytes : (1ull << 24) - 1);
         chunk = std::max<uint64_t>(1024, std::min<uint64_t>(chunk, (1ull << 24) - 1));
@@ -315,10 +315,10 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
             const int32_t plab = phis[s]->node_label[P.order[par]];
             D.cpi_cap[i] = std::min<uint64_t>(lab_deg(plab, P.lv[i].tdir == 1), (uint64_t)g->m);
             F.cpi_off[i] = L.take(4ull * (D.cand_cap[par] + 1ull));
-            F.cpi_idx[i] = L.take(4ull * std::max<uint64_t>(1, D.cpi_cap[i]));
+            F.cpi_idx[i] = L.take(8ull * std::max<uint64_t>(1, D.cpi_cap[i]));
         }
         for (int l = 1; l <= P.k - 2; l++) {
-            F.rows[l] = L.take(4ull * (2 * (l + 1) + 1) * chunk);
+            F.rows[l] = L.take(4ull * (2 * (l + 1) + 2) * chunk);
             F.wpre[l] = L.take(8ull * chunk);
         }
     }
@@ -382,7 +382,7 @@ int group_build(gfd_graph* g, Group* G, const Tables& T, bool refine, cudaStream
             D.cand[i] = (int32_t*)(base + F.cand[i]);
             if (i >= 1) {
                 D.cpi_off[i] = (uint32_t*)(base + F.cpi_off[i]);
-                D.cpi_idx[i] = (int32_t*)(base + F.cpi_idx[i]);
+                D.cpi_idx[i] = (int2*)(base + F.cpi_idx[i]);
             }
         }
         for (int l = 1; l <= P.k - 2; l++) {
