@@ -388,7 +388,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                     if (ok) {
                         const uint64_t row = (old >> ROW_SHIFT) + (excl >> ROW_SHIFT);
                         if (row < D->chunk) {
-                            const int nw = 2 * (i + 1) + 1;
+                            const int nw = 2 * (i + 1) + 2;
                             int32_t* dst = D->rows[i] + row * nw;
                             for (int q = 0; q <= i; q++) dst[q] = (int32_t)m[q];
                             if (l == 0) {
