@@ -107,8 +107,11 @@ int launch_and(const DevGraph& g, const AndJob* d_jobs, int njobs, cudaStream_t 
 int launch_compact(const DevGraph& g, const CompactJob* d_jobs, int njobs, cudaStream_t st);
 int launch_scatter(const DevGraph& g, const ScatterJob* d_jobs, int njobs, cudaStream_t st);
 int launch_prune(const DevGraph& g, const PruneJob* d_jobs, int njobs, cudaStream_t st);
-int launch_cpi(const DevGraph& g, const CpiJob* d_jobs, int njobs, uint32_t nchunks, int32_t* d_err,
-               cudaStream_t st);
+// Index edges in two launches: counts, offsets and per-job totals first (the
+// caller reads the totals back and allocates exactly), then the fill.
+int launch_cpi_count(const DevGraph& g, const CpiJob* d_jobs, int njobs, uint32_t nchunks, int32_t* d_err,
+                     uint32_t* d_totals, cudaStream_t st);
+int launch_cpi_fill(const DevGraph& g, const CpiJob* d_jobs, int njobs, cudaStream_t st);
 uint32_t compact_chunks(const DevGraph& g);
 uint32_t cpi_chunks(uint64_t max_parent_candidates);
 

@@ -422,6 +422,12 @@ __global__ void k_cpi_fill(DevGraph g, const CpiJob* __restrict__ jobs, int njob
     }
 }
 
+// number of index edges of each job (read back to size the index exactly)
+__global__ void k_cpi_totals(const CpiJob* __restrict__ jobs, int njobs, uint32_t* totals) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < njobs) totals[j] = jobs[j].off[*jobs[j].pcount];
+}
+
 int grid_warps(int sms_mult = 8) { return 152 * sms_mult; }
 
 int check_launch(const char* what) {
@@ -478,15 +484,21 @@ uint32_t cpi_chunks(uint64_t max_parent_candidates) {
     return (uint32_t)(max_parent_candidates / COMPACT_WORDS + 1);
 }
 
-int launch_cpi(const DevGraph& g, const CpiJob* d_jobs, int njobs, uint32_t nchunks, int32_t* d_err,
-               cudaStream_t st) {
+int launch_cpi_count(const DevGraph& g, const CpiJob* d_jobs, int njobs, uint32_t nchunks, int32_t* d_err,
+                     uint32_t* d_totals, cudaStream_t st) {
     if (njobs <= 0) return GFD_OK;
     k_cpi_count<<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs);
     const int grid = (int)std::min<uint64_t>((uint64_t)njobs * nchunks, 152 * 4);
     k_cpi_sums<<<grid, COMPACT_THREADS, 0, st>>>(d_jobs, njobs, nchunks);
     k_cpi_scan<<<grid, COMPACT_THREADS, 0, st>>>(d_jobs, njobs, nchunks, d_err);
+    k_cpi_totals<<<(njobs + 255) / 256, 256, 0, st>>>(d_jobs, njobs, d_totals);
+    return check_launch("k_cpi_count");
+}
+
+int launch_cpi_fill(const DevGraph& g, const CpiJob* d_jobs, int njobs, cudaStream_t st) {
+    if (njobs <= 0) return GFD_OK;
     k_cpi_fill<<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs);
-    return check_launch("k_cpi");
+    return check_launch("k_cpi_fill");
 }
 
 }  // namespace gfd

@@ -218,7 +218,10 @@ struct Group {
         size_t bm[MAXK], rank[MAXK], cand[MAXK], cpi_off[MAXK], cpi_idx[MAXK], rows[MAXK], wpre[MAXK];
     };
     std::vector<Off> offs;
-    size_t o_keybm = 0, o_keys = 0, o_tmp = 0, o_cmp_sums = 0, o_cpi_sums = 0;
+    size_t o_keybm = 0, o_keys = 0, o_tmp = 0, o_cmp_sums = 0, o_cpi_sums = 0, o_cpi_tot = 0;
+    uint8_t* cpi_base = nullptr;  // index edges, sized after counting
+    size_t cpi_bytes = 0;
+    size_t cpi_bound = 0;  // upper bound of cpi_bytes known at planning time
     size_t o_jobs = 0, o_and = 0, o_cmp = 0, o_sct = 0, o_prn = 0, o_cpi = 0, jobs_end = 0;
     uint32_t cmp_chunks = 1, cpi_nch = 1;
     size_t td_need = 0;
@@ -315,7 +318,7 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
             const int32_t plab = phis[s]->node_label[P.order[par]];
             D.cpi_cap[i] = std::min<uint64_t>(lab_deg(plab, P.lv[i].tdir == 1), (uint64_t)g->m);
             F.cpi_off[i] = L.take(4ull * (D.cand_cap[par] + 1ull));
-            F.cpi_idx[i] = L.take(8ull * std::max<uint64_t>(1, D.cpi_cap[i]));
+            G->cpi_bound += 8ull * std::max<uint64_t>(1, D.cpi_cap[i]) + 256;
         }
         for (int l = 1; l <= P.k - 2; l++) {
             F.rows[l] = L.take(4ull * (2 * (l + 1) + 2) * chunk);
@@ -349,6 +352,7 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
     G->cpi_nch = cpi_chunks(max_pcand);
     G->o_cmp_sums = L.take(4ull * G->cmp_chunks * std::max<size_t>(1, n_compact));
     G->o_cpi_sums = L.take(8ull * G->cpi_nch * std::max<size_t>(1, n_cpi));
+    G->o_cpi_tot = L.take(4ull * std::max<size_t>(1, n_cpi));
     // the region uploaded from the host: keys and job tables
     G->o_jobs = L.size;
     G->o_keys = L.take(sizeof(FilterKey) * std::max(1, nkeys));
@@ -382,7 +386,7 @@ int group_build(gfd_graph* g, Group* G, const Tables& T, bool refine, cudaStream
             D.cand[i] = (int32_t*)(base + F.cand[i]);
             if (i >= 1) {
                 D.cpi_off[i] = (uint32_t*)(base + F.cpi_off[i]);
-                D.cpi_idx[i] = (int2*)(base + F.cpi_idx[i]);
+                D.cpi_idx[i] = nullptr;  // allocated once the index edges are counted
             }
         }
         for (int l = 1; l <= P.k - 2; l++) {
@@ -538,7 +542,8 @@ int group_build(gfd_graph* g, Group* G, const Tables& T, bool refine, cudaStream
     return GFD_OK;
 }
 
-int group_launch(gfd_graph* g, Group* G, const Tables& T, cudaStream_t st, ProfEvents& prof, int64_t* launches) {
+int group_launch(gfd_graph* g, Group* G, const Tables& T, cudaMemPool_t pool, cudaStream_t st, ProfEvents& prof,
+                 int64_t* launches) {
     const DevGraph& dg = g->dg;
     uint8_t* base = G->base;
     prof.begin(PROF_FILTER, st);
@@ -570,9 +575,40 @@ int group_launch(gfd_graph* g, Group* G, const Tables& T, cudaStream_t st, ProfE
     }
     prof.end(PROF_REFINE, st);
     prof.begin(PROF_INDEX, st);
-    if (int rc = launch_cpi(dg, (const CpiJob*)(base + G->o_cpi), (int)G->cpi_jobs.size(), G->cpi_nch, T.err, st))
-        return rc;
-    launches[PROF_INDEX] += G->cpi_jobs.empty() ? 0 : 4;
+    const int ncpi = (int)G->cpi_jobs.size();
+    if (ncpi) {
+        CpiJob* d_cpi = (CpiJob*)(base + G->o_cpi);
+        uint32_t* d_tot = (uint32_t*)(base + G->o_cpi_tot);
+        if (int rc = launch_cpi_count(dg, d_cpi, ncpi, G->cpi_nch, T.err, d_tot, st)) return rc;
+        // size the index edges exactly: one read-back of the per-edge totals
+        std::vector<uint32_t> tot(ncpi);
+        GFD_CUDA(cudaMemcpyAsync(tot.data(), d_tot, 4ull * ncpi, cudaMemcpyDeviceToHost, st));
+        GFD_CUDA(cudaStreamSynchronize(st));
+        std::vector<size_t> at(ncpi);
+        size_t bytes = 256;
+        for (int j = 0; j < ncpi; j++) {
+            at[j] = bytes;
+            bytes = (bytes + 8ull * std::max<uint32_t>(1, tot[j]) + 255) & ~(size_t)255;
+        }
+        void* p = nullptr;
+        if (int rc = pool_alloc(pool, bytes, st, &p, "index edges")) return rc;
+        G->cpi_base = (uint8_t*)p;
+        G->cpi_bytes = bytes;
+        int j = 0;
+        for (int s = 0; s < G->n; s++)
+            for (int i = 1; i < G->plans[s].k; i++, j++) {
+                int2* idx = (int2*)(G->cpi_base + at[j]);
+                G->cpi_jobs[j].idx = idx;
+                G->cpi_jobs[j].cap = tot[j];
+                G->descs[s].cpi_idx[i] = idx;
+            }
+        GFD_CUDA(cudaMemcpyAsync(d_cpi, G->cpi_jobs.data(), sizeof(CpiJob) * ncpi, cudaMemcpyHostToDevice, st));
+        for (int s = 0; s < G->n; s++)
+            GFD_CUDA(cudaMemcpyAsync(&T.desc[G->slot[s]].cpi_idx, G->descs[s].cpi_idx, sizeof(G->descs[s].cpi_idx),
+                                     cudaMemcpyHostToDevice, st));
+        if (int rc = launch_cpi_fill(dg, d_cpi, ncpi, st)) return rc;
+        launches[PROF_INDEX] += 5;
+    }
     prof.end(PROF_INDEX, st);
     return GFD_OK;
 }
@@ -664,7 +700,9 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
     ProfEvents prof;
     if (int rc = prof.init((flags & GFD_FLAG_PROFILE) != 0)) return rc;
     int64_t launches[5] = {0, 0, 0, 0, 0};
-    if (int rc = group_launch(g, &G, T, st, prof, launches)) return rc;
+    const int lrc = group_launch(g, &G, T, pool, st, prof, launches);
+    fr.p.push_back(G.cpi_base);
+    if (lrc) return lrc;
     const EnumArgs A = enum_args(g, T);
     if (int rc = enum_init(A, st)) return rc;
     if (int rc = enum_run(A, persistent, use_graph, variant, st, prof.on ? prof.ev[2 * PROF_ENUM] : nullptr,
@@ -823,7 +861,10 @@ void session_free(gfd_session* S) {
     for (auto& d : S->done) gfd_result_free(d.second);
     for (auto& sl : S->slots) {
         if (sl.viol) cudaFreeAsync(sl.viol, S->st);
-        if (sl.group && --sl.group->live == 0 && sl.group->base) cudaFreeAsync(sl.group->base, S->st);
+        if (sl.group && --sl.group->live == 0) {
+            if (sl.group->base) cudaFreeAsync(sl.group->base, S->st);
+            if (sl.group->cpi_base) cudaFreeAsync(sl.group->cpi_base, S->st);
+        }
         sl.group.reset();
     }
     if (S->T.base) cudaFreeAsync(S->T.base, S->st);
@@ -878,7 +919,8 @@ int session_admit(gfd_session* S) {
         Group trial;
         const gfd_gfd* one[1] = {&R->phi};
         if (int rc = group_plan(S->g, one, 1, &S->opts, per_slot, &trial)) return rc;
-        const int64_t req_bytes = (int64_t)trial.bytes + (int64_t)(4ull * trial.plans[0].k * S->viol_cap);
+        const int64_t req_bytes =
+            (int64_t)(trial.bytes + trial.cpi_bound) + (int64_t)(4ull * trial.plans[0].k * S->viol_cap);
         const bool idle = S->used == 0 && take.empty();  // always admit into an idle device
         if (!idle && S->used + need + req_bytes > S->budget) break;
         need += req_bytes;
@@ -915,7 +957,9 @@ int session_admit(gfd_session* S) {
     if (int rc = group_build(S->g, G.get(), S->T, refine, S->st)) return rc;
     ProfEvents prof;
     int64_t launches[5] = {0, 0, 0, 0, 0};
-    if (int rc = group_launch(S->g, G.get(), S->T, S->st, prof, launches)) return rc;
+    const int lrc = group_launch(S->g, G.get(), S->T, S->pool, S->st, prof, launches);
+    S->used += (int64_t)G->cpi_bytes;
+    if (lrc) return lrc;
     return init_slots(enum_args(S->g, S->T), G->slot.data(), n, S->st);
 }
 
@@ -974,8 +1018,10 @@ int session_step(gfd_session* S, int32_t* n_advanced, int32_t* n_running, int32_
             S->used -= (int64_t)(4ull * sl.group->plans[sl.index].k * sl.viol_cap);
             if (--sl.group->live == 0) {
                 cudaFreeAsync(sl.group->base, S->st);
-                S->used -= (int64_t)sl.group->bytes;
+                if (sl.group->cpi_base) cudaFreeAsync(sl.group->cpi_base, S->st);
+                S->used -= (int64_t)(sl.group->bytes + sl.group->cpi_bytes);
                 sl.group->base = nullptr;
+                sl.group->cpi_base = nullptr;
             }
             sl.group.reset();
             sl.req.reset();
