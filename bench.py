@@ -324,10 +324,13 @@ def main():
     work = sum(r.stat(G.STAT_WORK) for r in stats)
     rows = sum(r.stat(G.STAT_ROWS) for r in stats)
     probes = stats[0].stat(G.STAT_PROBES)
+    enum_steps = stats[0].stat(G.STAT_STEPS)
     step_ms = float(np.mean(times))
     step_ms_max, value = aggregate(step_ms, matches, dist, "cuda")
 
-    # algorithmic bytes of one enumeration launch
+    # algorithmic bytes of one enumeration launch: 8 B per work item (its index
+    # edge), one 32 B sector per edge probe, 8 B per stored partial match, one
+    # 32 B sector per attribute a literal reads per match, 4k B per violation
     lit_bytes = sum(r.n_matches * 32 * literal_attrs(q) for r, q in zip(stats, qs))
     b_alg = 8 * work + 32 * probes + 8 * rows + lit_bytes + sum(4 * r.k * r.n_violations for r in stats)
     t_enum = float(np.mean(enum_ms)) / 1000.0
@@ -424,6 +427,7 @@ def main():
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,
                 "matches_per_step": matches, "violations_per_step": viols,
                 "work_items_per_step": work, "edge_probes_per_step": probes,
+                "enumeration_steps": enum_steps,
                 "gfds_rerun_for_violation_capacity": sum(r.stat(G.STAT_RERUN) for r in stats),
                 "step_ms_all": times, "enum_ms_all": enum_ms}
         print(json.dumps(line), flush=True)

@@ -146,6 +146,10 @@ struct Sched {
     uint64_t varena_used;
     int32_t vstride;
     int32_t pad2;
+    // next tile of the current step handed out to a warp that finished its
+    // first one (tiles below the warp count go to warps by index); on its own
+    // cache line, away from the fields every warp reads
+    alignas(128) uint32_t tile_next;
 };
 
 // device error codes (Sched::err, SlotState::err)

@@ -180,7 +180,7 @@ __device__ void expand_warps(const EnumArgs& A) {
     const DevGraph& g = A.g;
     const uint32_t total_tiles = *(volatile uint32_t*)&A.sched->total_tiles;
     uint64_t probes = 0;
-    for (uint64_t t = gwarp; t < total_tiles; t += nwarps) {
+    for (uint64_t t = gwarp; t < total_tiles;) {
         const int s = (int)warp_find(A.tile_base, 0, (uint64_t)A.n_slots, t, lane);
         const SlotDesc* __restrict__ D = A.slots + s;
         SlotState* S = A.state + s;
@@ -409,6 +409,9 @@ __device__ void expand_warps(const EnumArgs& A) {
             const unsigned long long tm = __reduce_add_sync(0xffffffffu, (unsigned)tile_matches);
             if (lane == 0 && tm) atomicAdd((unsigned long long*)&S->n_matches, tm);
         }
+        uint32_t nt = 0;
+        if (lane == 0) nt = atomicAdd(&A.sched->tile_next, 1u);
+        t = nwarps + __shfl_sync(0xffffffffu, nt, 0);
     }
     // probe statistics: one atomic per warp
     const unsigned long long p = __reduce_add_sync(0xffffffffu, (unsigned)min(probes, (uint64_t)0xffffffffu));
@@ -494,6 +497,7 @@ __device__ void control_step(const EnumArgs& A, bool first) {
     if (threadIdx.x == 0) {
         A.tile_base[A.n_slots] = carry_s;
         A.sched->total_tiles = carry_s;
+        A.sched->tile_next = 0;
         A.sched->active = active_s;
         A.sched->steps++;
         __threadfence();
