@@ -129,7 +129,7 @@ struct Sched {
     int32_t active;
     int32_t err;
     uint32_t total_tiles;
-    uint32_t tile;            // work items per tile
+    uint32_t tile;            // work items per tile in the current step
     uint32_t bar_count;       // grid barrier
     uint32_t bar_gen;
     uint32_t pad;

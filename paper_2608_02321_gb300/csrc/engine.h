@@ -123,7 +123,8 @@ struct EnumArgs {
     Sched* sched;
     uint32_t* tile_base;  // [n_slots + 1]
     int32_t n_slots;
-    int32_t tile;         // work items per tile
+    int32_t tile;         // largest number of work items per tile
+    int32_t n_warps;      // warps of the expansion grid (0: unknown, tiles of `tile`)
 };
 int enum_init(const EnumArgs& a, cudaStream_t st);
 // Mark slots [0, n) idle; start the listed slots (host ids) after their index is built.

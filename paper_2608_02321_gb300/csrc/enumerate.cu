@@ -179,6 +179,7 @@ __device__ void expand_warps(const EnumArgs& A) {
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const DevGraph& g = A.g;
     const uint32_t total_tiles = *(volatile uint32_t*)&A.sched->total_tiles;
+    const uint64_t tile = *(volatile uint32_t*)&A.sched->tile;  // work items per tile in this step
     uint64_t probes = 0;
     for (uint64_t t = gwarp; t < total_tiles;) {
         const int s = (int)warp_find(A.tile_base, 0, (uint64_t)A.n_slots, t, lane);
@@ -189,8 +190,8 @@ __device__ void expand_warps(const EnumArgs& A) {
         const int l = __ldcg(&S->cur);
         const int i = k == 1 ? 0 : l + 1;  // level being matched
         const bool last = i == k - 1;
-        const uint64_t wb = __ldcg((const unsigned long long*)&S->cb) + (t - __ldcg(A.tile_base + s)) * A.tile;
-        const uint64_t we = min(wb + (uint64_t)A.tile, (uint64_t)__ldcg((const unsigned long long*)&S->ce));
+        const uint64_t wb = __ldcg((const unsigned long long*)&S->cb) + (t - __ldcg(A.tile_base + s)) * tile;
+        const uint64_t we = min(wb + tile, (uint64_t)__ldcg((const unsigned long long*)&S->ce));
         const LevelPlan& LP = D->lv[i];
         const uint32_t* S0 = i > 0 ? D->cpi_off[i] : nullptr;
         const uint64_t* Sl = l >= 1 ? D->wpre[l] : nullptr;
@@ -436,9 +437,11 @@ __device__ void control_step(const EnumArgs& A, bool first) {
     __shared__ uint32_t carry_s;
     __shared__ int32_t active_s;
     __shared__ int32_t expired_s;
+    __shared__ unsigned long long work_s;
     if (threadIdx.x == 0) {
         carry_s = 0;
         active_s = 0;
+        work_s = 0;
         // bound the whole enumeration in time: past the limit every slot stops
         const uint64_t now = globaltimer_ns();
         if (first || A.sched->t_start == 0) A.sched->t_start = now;
@@ -448,7 +451,6 @@ __device__ void control_step(const EnumArgs& A, bool first) {
     __syncthreads();
     for (int base = 0; base < A.n_slots; base += CT) {
         const int s = base + threadIdx.x;
-        uint32_t tiles = 0;
         if (s < A.n_slots) {
             const SlotDesc* D = A.slots + s;
             SlotState* S = A.state + s;
@@ -482,10 +484,27 @@ __device__ void control_step(const EnumArgs& A, bool first) {
                 const uint64_t step = to_last ? max(D->chunk, (uint64_t)LAST_LEVEL_CHUNK) : D->chunk;
                 S->ce = min(S->cb + step, S->total[l]);
                 if (k > 1 && l + 1 <= k - 2) S->ctr[l + 1] = 0;
-                tiles = (uint32_t)((S->ce - S->cb + A.tile - 1) / A.tile);
                 S->st_work += S->ce - S->cb;
                 atomicAdd(&active_s, 1);
+                atomicAdd(&work_s, (unsigned long long)(S->ce - S->cb));
             }
+        }
+    }
+    __syncthreads();
+    // Tile size of this step: the largest (up to A.tile) that still gives every
+    // warp about four tiles, so that a step with little work (one slot at an
+    // intermediate level) is spread over all warps.
+    uint64_t tile = (uint64_t)A.tile;
+    if (A.n_warps > 0) {
+        const uint64_t per = work_s / (4ull * (uint64_t)A.n_warps);
+        tile = min(tile, max((uint64_t)32, (uint64_t)((per + 31) & ~(uint64_t)31)));
+    }
+    for (int base = 0; base < A.n_slots; base += CT) {
+        const int s = base + threadIdx.x;
+        uint32_t tiles = 0;
+        if (s < A.n_slots) {
+            const SlotState* S = A.state + s;
+            if (S->cur >= 0) tiles = (uint32_t)((S->ce - S->cb + tile - 1) / tile);
         }
         uint32_t excl, total;
         Scan(tmp).ExclusiveSum(tiles, excl, total);
@@ -497,6 +516,7 @@ __device__ void control_step(const EnumArgs& A, bool first) {
     if (threadIdx.x == 0) {
         A.tile_base[A.n_slots] = carry_s;
         A.sched->total_tiles = carry_s;
+        A.sched->tile = (uint32_t)tile;
         A.sched->tile_next = 0;
         A.sched->active = active_s;
         A.sched->steps++;
@@ -576,6 +596,7 @@ int launch_persistent(const EnumArgs& a, cudaStream_t st, int64_t* launches) {
     }
     const int grid = sms * per_sm;
     EnumArgs args = a;
+    args.n_warps = grid * (NT / 32);
     void* params[] = {&args};
     e = cudaLaunchCooperativeKernel((const void*)k_persistent<NT, MINB>, dim3(grid), dim3(NT), params, 0, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel");
@@ -593,8 +614,10 @@ int expand_grid() {
 }
 
 template <int NT, int MINB>
-int host_loop(const EnumArgs& a, bool use_graph, cudaStream_t st, int64_t* launches) {
+int host_loop(const EnumArgs& a0, bool use_graph, cudaStream_t st, int64_t* launches) {
     const int grid = expand_grid<NT, MINB>();
+    EnumArgs a = a0;
+    a.n_warps = grid * (NT / 32);
     int32_t* h_active = nullptr;
     cudaError_t e = cudaMallocHost(&h_active, sizeof(int32_t));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
@@ -708,8 +731,10 @@ int launch_split(const SlotDesc* slots, const int32_t* arena, uint64_t n, int32_
 namespace {
 
 template <int NT, int MINB>
-int capture_steps_t(const EnumArgs& a, int steps, cudaStream_t st, cudaGraph_t* graph, cudaGraphExec_t* exec) {
+int capture_steps_t(const EnumArgs& a0, int steps, cudaStream_t st, cudaGraph_t* graph, cudaGraphExec_t* exec) {
     const int grid = expand_grid<NT, MINB>();
+    EnumArgs a = a0;
+    a.n_warps = grid * (NT / 32);
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         for (int it = 0; it < steps; it++) {

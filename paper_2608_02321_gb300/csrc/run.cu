@@ -194,6 +194,7 @@ EnumArgs enum_args(const gfd_graph* g, const Tables& T) {
     A.tile_base = T.tiles;
     A.n_slots = T.max_slots;
     A.tile = T.tile;
+    A.n_warps = 0;
     return A;
 }
 
