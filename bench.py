@@ -300,7 +300,7 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
-    times, enum_ms, enum_launches, launches = [], [], 0, 0
+    times, enum_ms, enum_launches, launches, phase_ms = [], [], 0, 0, []
     stats = None
     for _ in range(args.steps):
         l2_flush.zero_()
@@ -317,6 +317,7 @@ def main():
         enum_ms.append(ms)
         enum_launches += 1
         launches += sum(res[0].profile(w)[1] for w in range(4))
+        phase_ms.append([res[0].profile(w)[0] for w in range(4)])
         stats = res
     clk = clocks.stop()
     matches = sum(r.n_matches for r in stats)
@@ -428,6 +429,8 @@ def main():
                 "matches_per_step": matches, "violations_per_step": viols,
                 "work_items_per_step": work, "edge_probes_per_step": probes,
                 "enumeration_steps": enum_steps,
+                "phase_ms": dict(zip(("filter", "refine", "index", "enumerate"),
+                                     np.mean(np.array(phase_ms), axis=0).round(2).tolist())),
                 "gfds_rerun_for_violation_capacity": sum(r.stat(G.STAT_RERUN) for r in stats),
                 "step_ms_all": times, "enum_ms_all": enum_ms}
         print(json.dumps(line), flush=True)

@@ -4,7 +4,8 @@
 //   graph:   out_off/in_off u32 [V+1]; out_adj/in_adj u32 [E] packed as
 //            (neighbour << lbits) | edge_label, rows sorted by neighbour;
 //            vinfo u32 [V] = vertex label (low 16 bits) | (self-loop label + 1) << 16
-//            (0 in the high half = no self-loop); attrs i32 [n_attrs][V].
+//            (0 in the high half = no self-loop); attrs i32 [n_attrs][V];
+//            sig u64x2 [V] = (out-, in-neighbourhood signature).
 //   index:   per (GFD, level) a candidate bitmap [nwords] u32, its exclusive
 //            popcount prefix [nwords] u32 (so rank(v) is O(1)), the sorted
 //            candidate list i32, and for every level i >= 1 the index edges of
@@ -49,7 +50,15 @@ struct DevGraph {
     const uint32_t* in_adj;
     const uint32_t* vinfo;
     const int32_t* attrs;
+    // neighbourhood signatures: sig[v].x has bit sig_bit(w) set for every
+    // out-neighbour w of v, sig[v].y for every in-neighbour; a clear bit proves
+    // that the edge is absent
+    const ulonglong2* sig;
 };
+
+// Signature bit of a vertex id: the top 6 bits of a Fibonacci (multiplicative)
+// hash.
+__host__ __device__ __forceinline__ uint32_t sig_bit(uint32_t v) { return (v * 0x9E3779B1u) >> 26; }
 
 // Candidate filter key (Section III.B step 1a-1b): label, degree lower bounds
 // (self-loops excluded on both sides) and the self-loop expectation.

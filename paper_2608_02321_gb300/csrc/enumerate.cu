@@ -283,9 +283,11 @@ __device__ void expand_warps(const EnumArgs& A) {
                         if (ok) {
                             j = cand_rank(D->bm[i], D->rank[i], v);
                             const uint32_t xp = m[LP.par];
-                            const int32_t gl =
-                                LP.tdir ? edge_label(g, xp, g.out_off[xp], g.out_off[xp + 1], v, g.in_off[v], g.in_off[v + 1])
-                                        : edge_label(g, v, g.out_off[v], g.out_off[v + 1], xp, g.in_off[xp], g.in_off[xp + 1]);
+                            const ulonglong2 sg = __ldg(g.sig + v);
+                            int32_t gl = NOEDGE;
+                            if (((LP.tdir ? sg.y : sg.x) >> sig_bit(xp)) & 1ull)
+                                gl = LP.tdir ? edge_label(g, xp, g.out_off[xp], g.out_off[xp + 1], v, g.in_off[v], g.in_off[v + 1])
+                                             : edge_label(g, v, g.out_off[v], g.out_off[v + 1], xp, g.in_off[xp], g.in_off[xp + 1]);
                             probes++;
                             ok = exp_ok(LP.tlab, gl);
                         }
@@ -295,14 +297,19 @@ __device__ void expand_warps(const EnumArgs& A) {
                         if (((LP.inj >> q) & 1u) && m[q] == v) ok = false;
                     // every other pattern pair, both directions (required edges first)
                     if (ok && LP.nchk > 0) {
+                        // v's signatures settle most pairs (absent edges) without
+                        // a search; the rest search the shorter adjacency list
+                        const ulonglong2 sg = __ldg(g.sig + v);
                         const uint32_t vo0 = g.out_off[v], vo1 = g.out_off[v + 1];
                         const uint32_t vi0 = g.in_off[v], vi1 = g.in_off[v + 1];
                         for (int c = 0; c < LP.nchk && ok; c++) {
                             if (c == skip) continue;
                             const uint32_t x = m[LP.chk_q[c]];
-                            int32_t gl;
-                            if (LP.chk_dir[c]) gl = edge_label(g, v, vo0, vo1, x, g.in_off[x], g.in_off[x + 1]);
-                            else gl = edge_label(g, x, g.out_off[x], g.out_off[x + 1], v, vi0, vi1);
+                            int32_t gl = NOEDGE;
+                            if (((LP.chk_dir[c] ? sg.x : sg.y) >> sig_bit(x)) & 1ull) {
+                                if (LP.chk_dir[c]) gl = edge_label(g, v, vo0, vo1, x, g.in_off[x], g.in_off[x + 1]);
+                                else gl = edge_label(g, x, g.out_off[x], g.out_off[x + 1], v, vi0, vi1);
+                            }
                             probes++;
                             ok = exp_ok(LP.chk_exp[c], gl);
                         }

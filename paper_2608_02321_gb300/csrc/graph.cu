@@ -82,6 +82,22 @@ __global__ void k_vinfo(const int32_t* vlabel, const uint32_t* out_off, const ui
     }
 }
 
+// One warp per vertex: OR of the signature bits of its out-neighbours (half 0)
+// or in-neighbours (half 1).
+__global__ void k_signature(const uint32_t* off, const uint32_t* adj, int32_t n, int32_t lbits, int half,
+                            unsigned long long* sig) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        unsigned long long b = 0;
+        for (uint32_t e = off[v] + lane; e < off[v + 1]; e += 32) b |= 1ull << sig_bit(adj[e] >> lbits);
+        const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)b);
+        const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(b >> 32));
+        if (lane == 0) sig[2 * v + half] = ((unsigned long long)hi << 32) | lo;
+    }
+}
+
 // keys[e] = (dst << 32) | src over the forward CSR, labels alongside.
 __global__ void k_transpose_keys(const uint32_t* off, const uint32_t* adj, int32_t n, int32_t lbits,
                                  uint32_t lmask, uint64_t* keys, uint8_t* labs) {
@@ -227,7 +243,9 @@ int graph_load(const gfd_graph_desc* d, const gfd_opts* o, gfd_graph** out) {
         (rc = dev_alloc(&attrs, (size_t)n * std::max(1, d->n_attrs), &g->bytes))) {
         return fail(rc);
     }
-    g->allocs = {out_off, in_off, out_adj, in_adj, vinfo, attrs};
+    unsigned long long* sig;
+    if ((rc = dev_alloc(&sig, 2 * (size_t)std::max(1, n), &g->bytes))) return fail(rc);
+    g->allocs = {out_off, in_off, out_adj, in_adj, vinfo, attrs, sig};
 
     TmpFree tmp;
     int64_t* d_off;
@@ -295,6 +313,8 @@ int graph_load(const gfd_graph_desc* d, const gfd_opts* o, gfd_graph** out) {
         tmp.ptrs.push_back(sstore);
         CK(cub::DeviceScan::ExclusiveSum(sstore, sb, deg, in_off, n + 1, st));
         k_pack_in<<<grid_for(m), 256, 0, st>>>(kb.Current(), lb.Current(), m, lbits, in_adj);
+        k_signature<<<grid_for((int64_t)n * 32), 256, 0, st>>>(out_off, out_adj, n, lbits, 0, sig);
+        k_signature<<<grid_for((int64_t)n * 32), 256, 0, st>>>(in_off, in_adj, n, lbits, 1, sig);
         CK(cudaGetLastError());
         if (have_in) {
             // the caller's reverse CSR must be exactly the transpose
@@ -370,6 +390,7 @@ int graph_load(const gfd_graph_desc* d, const gfd_opts* o, gfd_graph** out) {
     dg.in_adj = in_adj;
     dg.vinfo = vinfo;
     dg.attrs = attrs;
+    dg.sig = (const ulonglong2*)sig;
     *out = g;
     return GFD_OK;
 }
