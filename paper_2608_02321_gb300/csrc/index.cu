@@ -149,6 +149,16 @@ __global__ void __launch_bounds__(COMPACT_THREADS) k_compact_write(DevGraph g, c
 // scanned 32 edges at a time without idling lanes on short lists.
 constexpr uint32_t SHORT_LIST = 32;
 
+// A lane scanning a short list alone reads UNROLL entries per round and then
+// their UNROLL bitmap words, so that each round costs two dependent loads
+// rather than two per entry.
+constexpr int UNROLL = 4;
+
+__device__ __forceinline__ void load_group(const uint32_t* adj, uint32_t e, uint32_t e1, uint32_t (&p)[UNROLL]) {
+#pragma unroll
+    for (int t = 0; t < UNROLL; t++) p[t] = e + t < e1 ? __ldg(adj + e + t) : 0u;
+}
+
 __global__ void k_scatter(DevGraph g, const ScatterJob* __restrict__ jobs, int njobs) {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
@@ -168,11 +178,18 @@ __global__ void k_scatter(DevGraph g, const ScatterJob* __restrict__ jobs, int n
             }
             const bool is_long = e1 - e0 > SHORT_LIST;
             if (!is_long)
-                for (uint32_t e = e0; e < e1; e++) {
-                    const uint32_t p = adj[e];
-                    const uint32_t x = p >> g.lbits;
-                    if (label_ok(J.lab, (int32_t)(p & g.lmask)) && bit_of(J.filter, x))
-                        atomicOr(&J.marks[x >> 5], 1u << (x & 31));
+                for (uint32_t e = e0; e < e1; e += UNROLL) {
+                    uint32_t p[UNROLL], f[UNROLL];
+                    load_group(adj, e, e1, p);
+#pragma unroll
+                    for (int t = 0; t < UNROLL; t++)
+                        f[t] = e + t < e1 ? __ldg(J.filter + ((p[t] >> g.lbits) >> 5)) : 0u;
+#pragma unroll
+                    for (int t = 0; t < UNROLL; t++) {
+                        const uint32_t x = p[t] >> g.lbits;
+                        if (e + t < e1 && label_ok(J.lab, (int32_t)(p[t] & g.lmask)) && ((f[t] >> (x & 31)) & 1u))
+                            atomicOr(&J.marks[x >> 5], 1u << (x & 31));
+                    }
                 }
             for (uint32_t lm = __ballot_sync(0xffffffffu, is_long); lm; lm &= lm - 1) {
                 const int src = __ffs(lm) - 1;
@@ -192,9 +209,16 @@ __global__ void k_scatter(DevGraph g, const ScatterJob* __restrict__ jobs, int n
 // lane alone (short lists) or the whole warp (cooperative).
 __device__ __forceinline__ bool any_hit_serial(const DevGraph& g, const uint32_t* adj, uint32_t e0, uint32_t e1,
                                                int32_t lab, const uint32_t* bm) {
-    for (uint32_t e = e0; e < e1; e++) {
-        const uint32_t p = adj[e];
-        if (label_ok(lab, (int32_t)(p & g.lmask)) && bit_of(bm, p >> g.lbits)) return true;
+    for (uint32_t e = e0; e < e1; e += UNROLL) {
+        uint32_t p[UNROLL], w[UNROLL];
+        load_group(adj, e, e1, p);
+#pragma unroll
+        for (int t = 0; t < UNROLL; t++) w[t] = e + t < e1 ? __ldg(bm + ((p[t] >> g.lbits) >> 5)) : 0u;
+        bool hit = false;
+#pragma unroll
+        for (int t = 0; t < UNROLL; t++)
+            hit |= e + t < e1 && label_ok(lab, (int32_t)(p[t] & g.lmask)) && ((w[t] >> ((p[t] >> g.lbits) & 31)) & 1u);
+        if (hit) return true;
     }
     return false;
 }
@@ -269,9 +293,15 @@ __global__ void k_cpi_count(DevGraph g, const CpiJob* __restrict__ jobs, int njo
             const bool is_long = e1 - e0 > SHORT_LIST;
             uint32_t cnt = 0;
             if (!is_long)
-                for (uint32_t e = e0; e < e1; e++) {
-                    const uint32_t p = adj[e];
-                    cnt += label_ok(J.lab, (int32_t)(p & g.lmask)) && bit_of(J.cbm, p >> g.lbits);
+                for (uint32_t e = e0; e < e1; e += UNROLL) {
+                    uint32_t p[UNROLL], w[UNROLL];
+                    load_group(adj, e, e1, p);
+#pragma unroll
+                    for (int t = 0; t < UNROLL; t++) w[t] = e + t < e1 ? __ldg(J.cbm + ((p[t] >> g.lbits) >> 5)) : 0u;
+#pragma unroll
+                    for (int t = 0; t < UNROLL; t++)
+                        cnt += e + t < e1 && label_ok(J.lab, (int32_t)(p[t] & g.lmask)) &&
+                               ((w[t] >> ((p[t] >> g.lbits) & 31)) & 1u);
                 }
             for (uint32_t lm = __ballot_sync(0xffffffffu, is_long); lm; lm &= lm - 1) {
                 const int src = __ffs(lm) - 1;
@@ -380,16 +410,23 @@ __global__ void k_cpi_fill(DevGraph g, const CpiJob* __restrict__ jobs, int njob
             }
             const bool is_long = e1 - e0 > SHORT_LIST;
             if (!is_long)
-                for (uint32_t e = e0; e < e1; e++) {
-                    const uint32_t p = adj[e];
-                    const uint32_t x = p >> g.lbits;
-                    if (label_ok(J.lab, (int32_t)(p & g.lmask)) && bit_of(J.cbm, x)) {
-                        if (o < oend && o < J.cap) {
-                            const uint32_t word = J.cbm[x >> 5];
-                            J.idx[o] = make_int2((int32_t)(J.crank[x >> 5] + __popc(word & ((1u << (x & 31)) - 1))),
-                                                 (int32_t)x);
+                for (uint32_t e = e0; e < e1; e += UNROLL) {
+                    uint32_t p[UNROLL], w[UNROLL], rk[UNROLL];
+                    load_group(adj, e, e1, p);
+#pragma unroll
+                    for (int t = 0; t < UNROLL; t++) {
+                        const uint32_t x = p[t] >> g.lbits;
+                        w[t] = e + t < e1 ? __ldg(J.cbm + (x >> 5)) : 0u;
+                        rk[t] = e + t < e1 ? __ldg(J.crank + (x >> 5)) : 0u;
+                    }
+#pragma unroll
+                    for (int t = 0; t < UNROLL; t++) {
+                        const uint32_t x = p[t] >> g.lbits;
+                        if (e + t < e1 && label_ok(J.lab, (int32_t)(p[t] & g.lmask)) && ((w[t] >> (x & 31)) & 1u)) {
+                            if (o < oend && o < J.cap)
+                                J.idx[o] = make_int2((int32_t)(rk[t] + __popc(w[t] & ((1u << (x & 31)) - 1))), (int32_t)x);
+                            o++;
                         }
-                        o++;
                     }
                 }
             for (uint32_t lm = __ballot_sync(0xffffffffu, is_long); lm; lm &= lm - 1) {
