@@ -192,6 +192,13 @@ int32_t gfd_result_arity(const gfd_result *r);
  * copy to the host happen on the first call. NULL on error (see
  * gfd_last_error) or when there are no violations. */
 const int32_t *gfd_result_tuples(gfd_result *r);
+/* The same tuples written straight into caller-owned host memory `out` of
+ * `capacity` int32 (at least n_violations * k), without a copy owned by the
+ * result: the device sorts them and copies them to `out` on every call that
+ * comes before a gfd_result_tuples call (after one, they are copied from the
+ * result's buffer). Returns GFD_OK, GFD_ERR_INVALID_ARG (NULL or too small a
+ * buffer), GFD_ERR_OUT_OF_MEMORY or a CUDA error code. */
+int gfd_result_copy_tuples(gfd_result *r, int32_t *out, uint64_t capacity);
 /* Device time in milliseconds spent in kernel class `which` (0 candidate
  * filter, 1 refinement, 2 index build, 3 enumeration, 4 result sort) and the
  * number of launches, when GFD_FLAG_PROFILE was set; else 0. */

@@ -83,6 +83,7 @@ _SIGS = {
     "gfd_result_violations": (C.c_uint64, [C.c_void_p]),
     "gfd_result_arity": (C.c_int32, [C.c_void_p]),
     "gfd_result_tuples": (C.c_void_p, [C.c_void_p]),
+    "gfd_result_copy_tuples": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64]),
     "gfd_result_profile": (C.c_double, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
     "gfd_result_stat": (C.c_uint64, [C.c_void_p, C.c_int32]),
     "gfd_result_free": (None, [C.c_void_p]),
@@ -215,13 +216,10 @@ class Result:
     def violations(self) -> np.ndarray:
         """[n_violations, k] int32, lexicographically sorted (sorted on the device)."""
         n, k = self.n_violations, self.k
-        p = _lib.gfd_result_tuples(self._h)
-        if n == 0:
-            return np.zeros((0, k), dtype=np.int32)
-        if not p:
-            _check(GFD_ERR_CUDA)
-        buf = (C.c_int32 * (n * k)).from_address(p)
-        return np.frombuffer(buf, dtype=np.int32).reshape(n, k).copy()
+        out = np.empty((n, k), dtype=np.int32)
+        if n:
+            _check(_lib.gfd_result_copy_tuples(self._h, out.ctypes.data_as(C.c_void_p), C.c_uint64(n * k)))
+        return out
 
     def profile(self, which: int):
         """(device milliseconds, launches) of a kernel class (needs FLAG_PROFILE)."""

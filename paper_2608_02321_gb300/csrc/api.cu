@@ -1,3 +1,4 @@
+#include <cstring>
 // C-ABI entry points declared in include/gfd.h.
 #include <cstdarg>
 #include <cstdio>
@@ -83,7 +84,26 @@ const int32_t* gfd_result_tuples(gfd_result* r) {
         return nullptr;
     }
     if (gfd::result_fetch(r) != GFD_OK) return nullptr;
-    return r->tuples.empty() ? nullptr : r->tuples.data();
+    return r->tuples.get();
+}
+
+int gfd_result_copy_tuples(gfd_result* r, int32_t* out, uint64_t capacity) {
+    if (!r || (!out && r->n_viol > 0)) {
+        gfd::set_error(GFD_ERR_INVALID_ARG, "gfd_result_copy_tuples: NULL argument");
+        return GFD_ERR_INVALID_ARG;
+    }
+    const uint64_t need = r->n_viol * (uint64_t)r->k;
+    if (capacity < need) {
+        gfd::set_error(GFD_ERR_INVALID_ARG, "gfd_result_copy_tuples: capacity %llu < %llu ints",
+                       (unsigned long long)capacity, (unsigned long long)need);
+        return GFD_ERR_INVALID_ARG;
+    }
+    if (need == 0) return GFD_OK;
+    if (r->fetched) {
+        memcpy(out, r->tuples.get(), 4 * need);
+        return GFD_OK;
+    }
+    return gfd::result_sort_copy(r, out);
 }
 
 double gfd_result_profile(const gfd_result* r, int32_t which, int64_t* launches) {

@@ -3,6 +3,7 @@
 
 #include <mutex>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include "common.cuh"
@@ -47,7 +48,7 @@ struct gfd_result {
     uint64_t n_viol = 0;
     int32_t* d_viol = nullptr;  // device, unsorted, owned by the result
     bool fetched = false;
-    std::vector<int32_t> tuples;
+    std::unique_ptr<int32_t[]> tuples;  // host copy made by gfd_result_tuples
     double prof_ms[5] = {0, 0, 0, 0, 0};
     int64_t prof_launch[5] = {0, 0, 0, 0, 0};
     uint64_t stat[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -156,6 +157,9 @@ int session_submit(gfd_session* s, const gfd_gfd* phi, int64_t* id);
 int session_step(gfd_session* s, int32_t* n_advanced, int32_t* n_running, int32_t* n_queued);
 int session_next_result(gfd_session* s, int64_t* id, gfd_result** out);
 int autotune(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opts* o, gfd_opts* best);
+// Sort the violation tuples on the device and copy them to dst (host memory,
+// n_viol * k ints); result_fetch does this into the result's own buffer.
+int result_sort_copy(gfd_result* r, int32_t* dst);
 int result_fetch(gfd_result* r);
 
 }  // namespace gfd

@@ -1139,12 +1139,25 @@ __global__ void k_gather_rows(const int32_t* t, int k, const uint32_t* perm, uin
 int result_fetch(gfd_result* r) {
     if (r->fetched) return GFD_OK;
     const uint64_t n = r->n_viol;
-    const int k = r->k;
-    r->tuples.assign(n * k, 0);
-    if (n == 0) {
-        r->fetched = true;
-        return GFD_OK;
+    if (n > 0) {
+        r->tuples.reset(new (std::nothrow) int32_t[n * r->k]);
+        if (!r->tuples) {
+            set_error(GFD_ERR_OUT_OF_MEMORY, "violation tuples: %llu host bytes", (unsigned long long)(4ull * n * r->k));
+            return GFD_ERR_OUT_OF_MEMORY;
+        }
+        if (int rc = result_sort_copy(r, r->tuples.get())) {
+            r->tuples.reset();
+            return rc;
+        }
     }
+    r->fetched = true;
+    return GFD_OK;
+}
+
+int result_sort_copy(gfd_result* r, int32_t* dst) {
+    const uint64_t n = r->n_viol;
+    const int k = r->k;
+    if (n == 0) return GFD_OK;
     cudaStream_t st = r->stream;
     uint32_t *p0, *p1;
     uint64_t *k0, *k1;
@@ -1174,7 +1187,7 @@ int result_fetch(gfd_result* r) {
     }
     if (rc == GFD_OK) {
         k_gather_rows<<<grid, 256, 0, st>>>(r->d_viol, k, pb.Current(), n, sorted);
-        cudaError_t e = cudaMemcpyAsync(r->tuples.data(), sorted, 4 * n * k, cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaMemcpyAsync(dst, sorted, 4 * n * k, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = cuda_fail(e, "violation copy");
     }
@@ -1184,7 +1197,6 @@ int result_fetch(gfd_result* r) {
     cudaFreeAsync(k0, st);
     cudaFreeAsync(k1, st);
     cudaFreeAsync(sorted, st);
-    if (rc == GFD_OK) r->fetched = true;
     return rc;
 }
 
