@@ -681,7 +681,15 @@ __global__ void k_split(const SlotDesc* slots, const int32_t* arena, uint64_t n,
         const int32_t* rec = arena + r * stride;
         const int s = rec[0];
         const int k = slots[s].k;
-        const uint64_t pos = atomicAdd(&cursor[s], 1ull);
+        // one atomic per group of lanes with the same slot (records of one
+        // slot arrive in runs, so a warp usually needs one or two)
+        const int lane = threadIdx.x & 31;
+        const uint32_t peers = __match_any_sync(__activemask(), s);
+        const int leader = __ffs(peers) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(&cursor[s], (unsigned long long)__popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        const uint64_t pos = base + __popc(peers & ((1u << lane) - 1u));
         int32_t* dst = lists[s] + pos * k;
         for (int q = 0; q < k; q++) dst[q] = rec[1 + q];
     }
