@@ -107,13 +107,16 @@ __device__ __forceinline__ uint32_t find_row(const uint64_t* S, uint64_t n, uint
     return (uint32_t)lo;
 }
 
-// Loads for the searches: index offsets are read-only during the enumeration
-// (read-only cache); frontier prefixes and the per-step tile prefix are
-// rewritten between steps (L2 only).
-__device__ __forceinline__ uint32_t ld_front(const uint32_t* p) { return __ldcg(p); }
-__device__ __forceinline__ uint64_t ld_front(const uint64_t* p) {
-    return __ldcg((const unsigned long long*)p);
-}
+// Loads of data rewritten between steps (frontier rows and prefixes, the
+// per-step tile prefix): plain weak loads, which may be served from L1. In the
+// persistent kernel the grid barrier orders them after the previous step's
+// writes: every writer's block fences at gpu scope before arriving, each
+// block's thread 0 fences at gpu scope after observing the release, and the
+// block barrier orders the block's other threads after that fence, so by the
+// PTX memory model the loads observe the writes (the pattern of a cooperative
+// grid synchronisation). In the host-driven loop the kernel boundary orders them.
+__device__ __forceinline__ uint32_t ld_front(const uint32_t* p) { return *p; }
+__device__ __forceinline__ uint64_t ld_front(const uint64_t* p) { return *p; }
 
 // r in [lo, hi) with S[r] <= w < S[r+1]: the search limited to the rows of a tile.
 __device__ __forceinline__ uint32_t find_row_in(const uint32_t* S, uint32_t lo, uint32_t hi, uint64_t w) {
@@ -205,8 +208,11 @@ __device__ void expand_warps(const EnumArgs& A) {
                 rlo = warp_find(S0, 0, nrows, wb, lane);
                 rhi1 = warp_find(S0, rlo, nrows, we - 1, lane) + 1;
             } else {
+                // stored rows all have fan-out >= 1, so the window search never
+                // runs past the tile's last row: the end of the row range need
+                // not be searched
                 rlo = warp_find(Sl, 0, nrows, wb, lane);
-                rhi1 = warp_find(Sl, rlo, nrows, we - 1, lane) + 1;
+                rhi1 = (uint32_t)nrows;
             }
         }
         uint64_t tile_matches = 0;
@@ -258,9 +264,9 @@ __device__ void expand_warps(const EnumArgs& A) {
                         m[0] = (uint32_t)D->cand[0][r];
                     } else {
                         rowp = rows_l + (uint64_t)r * rw;
-                        for (int q = 0; q <= l; q++) m[q] = (uint32_t)__ldcg(rowp + q);
-                        choice = __ldcg(rowp + 2 * (l + 1));
-                        ent = (uint64_t)(uint32_t)__ldcg(rowp + 2 * (l + 1) + 1) + o;
+                        for (int q = 0; q <= l; q++) m[q] = (uint32_t)rowp[q];
+                        choice = rowp[2 * (l + 1)];
+                        ent = (uint64_t)(uint32_t)rowp[2 * (l + 1) + 1] + o;
                     }
                     int skip = -1;
                     if (choice == 0) {
@@ -365,7 +371,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                 if (ok) {
                     const LevelPlan& L2 = D->lv[i + 1];
                     const int pn = L2.par;
-                    const uint32_t ppn = pn == i ? (uint32_t)j : (l == 0 ? r : (uint32_t)__ldcg(rowp + l + 1 + pn));
+                    const uint32_t ppn = pn == i ? (uint32_t)j : (l == 0 ? r : (uint32_t)rowp[l + 1 + pn]);
                     const uint32_t* co = D->cpi_off[i + 1];
                     nbase = __ldg(co + ppn);
                     fo = __ldg(co + ppn + 1) - nbase;
@@ -402,7 +408,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                             if (l == 0) {
                                 dst[i + 1] = (int32_t)r;
                             } else {
-                                for (int q = 0; q <= l; q++) dst[i + 1 + q] = __ldcg(rowp + l + 1 + q);
+                                for (int q = 0; q <= l; q++) dst[i + 1 + q] = rowp[l + 1 + q];
                             }
                             dst[i + 1 + i] = j;
                             dst[2 * (i + 1)] = gen;
