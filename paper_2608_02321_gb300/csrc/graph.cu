@@ -282,6 +282,13 @@ int graph_load(const gfd_graph_desc* d, const gfd_opts* o, gfd_graph** out) {
     k_pack_rows<<<grid_for((int64_t)n * 32), 256, 0, st>>>(d_off, d_nbr, d_lab, n, lbits, out_off, out_adj, d_bad);
     k_vinfo<<<grid_for(n), 256, 0, st>>>(d_vl, out_off, out_adj, n, lbits, lmask, vinfo, d_bad);
     CK(cudaGetLastError());
+    // the kernels below index arrays by neighbour id: stop here on a bad row
+    CK(cudaMemcpyAsync(&bad, d_bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (bad) {
+        set_error(GFD_ERR_INVALID_ARG, "gfd_graph_load: forward CSR:%s", bad_text(bad).c_str());
+        return fail(GFD_ERR_INVALID_ARG);
+    }
 
     // reverse CSR: stable radix sort of (dst, src) keys
     {
