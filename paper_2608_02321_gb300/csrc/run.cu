@@ -282,10 +282,13 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
     G->descs.assign(n, SlotDesc{});
     G->offs.resize(n);
     for (int lvl = 0; lvl < MAXK; lvl++) {
-        size_t c = 0;
+        size_t c = 0, b = 0;
         for (int s = 0; s < n; s++)
-            if (lvl < G->plans[s].k) c += G->plans[s].td[lvl].size();
-        G->td_need = std::max(G->td_need, c);
+            if (lvl < G->plans[s].k) {
+                c += G->plans[s].td[lvl].size();
+                b += G->plans[s].bu[lvl].size();
+            }
+        G->td_need = std::max(G->td_need, std::max(c, b));
     }
     for (int s = 0; s < n; s++) {
         const HostPlan& P = G->plans[s];
@@ -338,11 +341,12 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
         n_and += P.k;
         n_compact += P.k;
         for (int i = 0; i < P.k; i++) {
-            n_sct += refine ? P.td[i].size() : 0;
-            const bool pr = refine && !P.bu[i].empty();
+            n_sct += refine ? P.td[i].size() + P.bu[i].size() : 0;
+            const bool pr = refine && !P.bu[i].empty();   // bottom-up: an AND and a gather at most
             const bool tdg = refine && !P.td[i].empty();  // at most one top-down gather per level
             n_prn += pr + tdg;
-            n_compact += pr + tdg;
+            n_and += pr;
+            n_compact += 2 * pr + tdg;
         }
     }
     G->cmp_chunks = compact_chunks(g->dg);
@@ -477,28 +481,63 @@ int group_build(gfd_graph* g, Group* G, const Tables& T, bool refine, cudaStream
                 G->phases.push_back({1, c1, G->compact_jobs.size() - c1});
             }
         }
-        // bottom-up, reverse level order
+        // bottom-up, reverse level order; each constraint from a later level
+        // is applied in the cheaper direction, as top-down
         for (int lvl = maxk - 1; lvl >= 0; lvl--) {
-            size_t p0 = G->prune_jobs.size(), c0 = G->compact_jobs.size();
+            size_t a0 = G->and_jobs.size(), c0 = G->compact_jobs.size(), s0 = G->scatter_jobs.size();
+            size_t p0 = G->prune_jobs.size();
+            size_t tmp_used = 0;
+            std::vector<int> gathered;
             for (int s = 0; s < n; s++) {
                 const HostPlan& P = G->plans[s];
                 if (lvl >= P.k || P.bu[lvl].empty()) continue;
+                AndJob A{};
+                A.bm = G->descs[s].bm[lvl];
+                A.src = G->descs[s].bm[lvl];
                 PruneJob J{};
                 J.cand = G->descs[s].cand[lvl];
                 J.count = state_ncand(s, lvl);
                 J.bm = G->descs[s].bm[lvl];
                 for (const Con& c : P.bu[lvl]) {
-                    J.con_bm[J.ncon] = G->descs[s].bm[c.q];
-                    J.con_dir[J.ncon] = c.dir;
-                    J.con_lab[J.ncon] = c.lab;
-                    J.ncon++;
+                    const int32_t lq = P.key[c.q].label, li = P.key[lvl].label;
+                    if (td_gather_cheaper(g, lq, li, c.dir)) {
+                        J.con_bm[J.ncon] = G->descs[s].bm[c.q];
+                        J.con_dir[J.ncon] = c.dir;
+                        J.con_lab[J.ncon] = c.lab;
+                        J.ncon++;
+                        continue;
+                    }
+                    uint32_t* marks = (uint32_t*)(base + G->o_tmp + 4ull * nwords * tmp_used++);
+                    ScatterJob S{};
+                    S.qcand = G->descs[s].cand[c.q];
+                    S.qcount = state_ncand(s, c.q);
+                    S.filter = G->descs[s].bm[lvl];
+                    S.marks = marks;
+                    S.scan_out = c.dir ? 0 : 1;
+                    S.lab = c.lab;
+                    G->scatter_jobs.push_back(S);
+                    A.tmp[A.ntmp++] = marks;
                 }
-                G->prune_jobs.push_back(J);
-                G->compact_jobs.push_back(compact_job(s, lvl));
+                if (A.ntmp) {
+                    G->and_jobs.push_back(A);
+                    G->compact_jobs.push_back(compact_job(s, lvl));
+                }
+                if (J.ncon) {
+                    G->prune_jobs.push_back(J);
+                    gathered.push_back(s);
+                }
             }
-            if (G->prune_jobs.size() > p0) {
-                G->phases.push_back({3, p0, G->prune_jobs.size() - p0});
+            if (tmp_used) G->phases.push_back({4, 0, tmp_used});
+            if (G->scatter_jobs.size() > s0) G->phases.push_back({2, s0, G->scatter_jobs.size() - s0});
+            if (G->and_jobs.size() > a0) {
+                G->phases.push_back({0, a0, G->and_jobs.size() - a0});
                 G->phases.push_back({1, c0, G->compact_jobs.size() - c0});
+            }
+            if (!gathered.empty()) {
+                const size_t c1 = G->compact_jobs.size();
+                for (int s : gathered) G->compact_jobs.push_back(compact_job(s, lvl));
+                G->phases.push_back({3, p0, G->prune_jobs.size() - p0});
+                G->phases.push_back({1, c1, G->compact_jobs.size() - c1});
             }
         }
     }
@@ -519,7 +558,17 @@ int group_build(gfd_graph* g, Group* G, const Tables& T, bool refine, cudaStream
             J.csum = (uint64_t*)(base + G->o_cpi_sums + 8ull * G->cpi_nch * G->cpi_jobs.size());
             G->cpi_jobs.push_back(J);
         }
-    // one host image of keys and job tables
+    // one host image of keys and job tables (each table within its region)
+    const size_t need[6] = {sizeof(FilterKey) * G->keys.size(), sizeof(AndJob) * G->and_jobs.size(),
+                            sizeof(CompactJob) * G->compact_jobs.size(), sizeof(ScatterJob) * G->scatter_jobs.size(),
+                            sizeof(PruneJob) * G->prune_jobs.size(), sizeof(CpiJob) * G->cpi_jobs.size()};
+    const size_t at[7] = {G->o_keys, G->o_and, G->o_cmp, G->o_sct, G->o_prn, G->o_cpi, G->jobs_end};
+    for (int t = 0; t < 6; t++)
+        if (at[t] + need[t] > at[t + 1]) {
+            set_error(GFD_ERR_CUDA, "internal: job table %d needs %zu bytes, region holds %zu", t, need[t],
+                      at[t + 1] - at[t]);
+            return GFD_ERR_CUDA;
+        }
     std::vector<uint8_t> img(G->jobs_end - G->o_jobs, 0);
     auto put = [&](size_t off, const void* p, size_t bytes) {
         if (bytes) memcpy(img.data() + (off - G->o_jobs), p, bytes);
