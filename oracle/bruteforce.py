@@ -5,6 +5,8 @@ of vertices to pin the C oracle: try every injective h : V_Q → V (P(V, k) maps
 keep those that preserve vertex labels and have (a, b) ∈ E_Q ⇔ (h(a), h(b)) ∈ E
 for every ordered pair of pattern nodes (self-pairs included) with equal edge
 labels, then apply the literal semantics. No ordering, no pruning.
+With induced=False only the pairs in E_Q are required (non-induced mode: pairs
+outside E_Q, self-pairs included, are unconstrained).
 """
 from __future__ import annotations
 
@@ -31,7 +33,7 @@ def _holds(lit, h, attrs):
     return vb != ABSENT and va == vb
 
 
-def brute_force(graph, gfd):
+def brute_force(graph, gfd, induced: bool = True):
     """(n_matches, sorted violations [n, k])."""
     E = _edge_map(graph)
     k = gfd.k
@@ -48,6 +50,8 @@ def brute_force(graph, gfd):
             for b in range(k):
                 ql = qe.get((a, b))
                 gl = E.get((h[a], h[b]))
+                if ql is None and not induced:
+                    continue
                 if (ql is None) != (gl is None):
                     ok = False
                 elif ql is not None and ql != WILDCARD and ql != gl:

@@ -20,6 +20,13 @@
  *   literal fails). The output is the number of matches and the violating
  *   tuples (h(x_0), ..., h(x_{k-1})) sorted lexicographically.
  *
+ *   Non-induced mode (og_validate_mode with induced = 0): the matching of Bi et
+ *   al. that Section III contrasts with the paper's definition, and the reading
+ *   of the evaluation's path query (Section V: accounts 0 and 2 "may or may not"
+ *   be connected). Only the pairs in E_Q constrain h: (a, b) ∈ E_Q implies
+ *   (h(a), h(b)) ∈ E with an agreeing label; pairs outside E_Q (self-pairs
+ *   included) are unconstrained. Injectivity and vertex labels stay.
+ *
  * Algorithm: Ullmann-style backtracking (Section III's description of the
  * generic scheme). Node 0 first, then breadth-first over the undirected
  * skeleton of Q visiting neighbours by increasing node id. Level 0 tries every
@@ -173,9 +180,14 @@ static int og_label_ok(int32_t want, int32_t have) {
     return want == OG_WILDCARD || want == have;
 }
 
+/* Matching mode of the call running on this thread: 1 induced, 0 non-induced. */
+static _Thread_local int og_induced = 1;
+
 /* Do pattern edge label `ql` (or OG_NOEDGE) and graph edge label `gl` (or
- * OG_NOEDGE) agree? Both absent, or both present with equal label / wildcard. */
+ * OG_NOEDGE) agree? Both absent, or both present with equal label / wildcard;
+ * in non-induced mode an absent pattern pair accepts anything. */
 static int og_pair_ok(int32_t ql, int32_t gl) {
+    if (!og_induced && ql == OG_NOEDGE) return 1;
     if (ql == OG_NOEDGE) return gl == OG_NOEDGE;
     if (gl == OG_NOEDGE) return 0;
     return og_label_ok(ql, gl);
@@ -251,21 +263,23 @@ static void og_extend(og_state *s, int i) {
     }
 }
 
-/* Validate one GFD. roots: the vertices tried for pattern node 0 (NULL: all of V).
+/* Validate one GFD; induced = 1 is the paper's matching, 0 the non-induced
+ * mode described at the top. roots: the vertices tried for pattern node 0 (NULL: all of V).
  * seconds > 0 bounds the run: the root being searched when time runs out is
  * dropped together with its matches, and *roots_done tells how many roots were
  * searched to the end (all of them when there is no bound).
  * Returns 0 on success, 1 for a malformed or disconnected pattern. On success the
  * caller owns *viol_out (free with og_free). */
-int og_validate_budget(const og_graph *g, const og_gfd *q, const int32_t *roots, int64_t n_roots,
-                       double seconds, uint64_t *n_matches, int32_t **viol_out, int64_t *n_viol,
-                       int64_t *roots_done) {
+int og_validate_mode(const og_graph *g, const og_gfd *q, int induced, const int32_t *roots, int64_t n_roots,
+                     double seconds, uint64_t *n_matches, int32_t **viol_out, int64_t *n_viol,
+                     int64_t *roots_done) {
     og_state s;
     int32_t placed[OG_MAXK];
     int i, j, head, tail;
     int64_t r;
     memset(&s, 0, sizeof(s));
     s.g = g; s.q = q;
+    og_induced = induced ? 1 : 0;
     if (q->k < 1 || q->k > OG_MAXK) return 1;
     for (i = 0; i < OG_MAXK; i++)
         for (j = 0; j < OG_MAXK; j++) s.qedge[i][j] = OG_NOEDGE;
@@ -325,9 +339,16 @@ int og_validate_budget(const og_graph *g, const og_gfd *q, const int32_t *roots,
     return 0;
 }
 
+/* The paper's (induced) matching, bounded in time as og_validate_mode. */
+int og_validate_budget(const og_graph *g, const og_gfd *q, const int32_t *roots, int64_t n_roots,
+                       double seconds, uint64_t *n_matches, int32_t **viol_out, int64_t *n_viol,
+                       int64_t *roots_done) {
+    return og_validate_mode(g, q, 1, roots, n_roots, seconds, n_matches, viol_out, n_viol, roots_done);
+}
+
 int og_validate(const og_graph *g, const og_gfd *q, const int32_t *roots, int64_t n_roots,
                 uint64_t *n_matches, int32_t **viol_out, int64_t *n_viol) {
-    return og_validate_budget(g, q, roots, n_roots, 0.0, n_matches, viol_out, n_viol, NULL);
+    return og_validate_mode(g, q, 1, roots, n_roots, 0.0, n_matches, viol_out, n_viol, NULL);
 }
 
 /* --------------------------------------------------------------- sorting */

@@ -64,6 +64,10 @@ def bind_library(path: str):
     lib.og_validate_budget.argtypes = [C.c_void_p, C.POINTER(_Gfd), C.c_void_p, C.c_int64, C.c_double,
                                        C.POINTER(C.c_uint64), C.POINTER(C.c_void_p),
                                        C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    lib.og_validate_mode.restype = C.c_int
+    lib.og_validate_mode.argtypes = [C.c_void_p, C.POINTER(_Gfd), C.c_int, C.c_void_p, C.c_int64, C.c_double,
+                                     C.POINTER(C.c_uint64), C.POINTER(C.c_void_p),
+                                     C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     lib.og_free.argtypes = [C.c_void_p]
     return lib
 
@@ -140,18 +144,26 @@ def _gfd_struct(gfd):
     return s, keep
 
 
-def _run(og: OracleGraph, gfd, roots):
+def _run(og: OracleGraph, gfd, roots, induced: bool = True):
     lib = og._lib
     s, keep = _gfd_struct(gfd)
     nm = C.c_uint64(0)
     vp = C.c_void_p(None)
     nv = C.c_int64(0)
     if roots is None:
-        rc = lib.og_validate(og._h, C.byref(s), None, 0, C.byref(nm), C.byref(vp), C.byref(nv))
+        if induced:
+            rc = lib.og_validate(og._h, C.byref(s), None, 0, C.byref(nm), C.byref(vp), C.byref(nv))
+        else:
+            rc = lib.og_validate_mode(og._h, C.byref(s), 0, None, 0, 0.0, C.byref(nm), C.byref(vp),
+                                      C.byref(nv), None)
     else:
         r = np.ascontiguousarray(roots, dtype=np.int32)
-        rc = lib.og_validate(og._h, C.byref(s), _ptr(r), int(r.shape[0]), C.byref(nm),
-                             C.byref(vp), C.byref(nv))
+        if induced:
+            rc = lib.og_validate(og._h, C.byref(s), _ptr(r), int(r.shape[0]), C.byref(nm),
+                                 C.byref(vp), C.byref(nv))
+        else:
+            rc = lib.og_validate_mode(og._h, C.byref(s), 0, _ptr(r), int(r.shape[0]), 0.0, C.byref(nm),
+                                      C.byref(vp), C.byref(nv), None)
     if rc != 0:
         raise ValueError("oracle rejected the GFD (malformed or disconnected pattern)")
     k = gfd.k
@@ -167,7 +179,7 @@ def _run(og: OracleGraph, gfd, roots):
     return int(nm.value), out
 
 
-def count_within(og: OracleGraph, gfd, roots, seconds: float):
+def count_within(og: OracleGraph, gfd, roots, seconds: float, induced: bool = True):
     """(matches, roots searched to the end) for the given roots, stopping after
     about `seconds`; the root in progress at the deadline is not counted."""
     lib = og._lib
@@ -177,8 +189,8 @@ def count_within(og: OracleGraph, gfd, roots, seconds: float):
     nv = C.c_int64(0)
     done = C.c_int64(0)
     r = np.ascontiguousarray(roots, dtype=np.int32)
-    rc = lib.og_validate_budget(og._h, C.byref(s), _ptr(r), int(r.shape[0]), float(seconds), C.byref(nm),
-                                C.byref(vp), C.byref(nv), C.byref(done))
+    rc = lib.og_validate_mode(og._h, C.byref(s), 1 if induced else 0, _ptr(r), int(r.shape[0]),
+                              float(seconds), C.byref(nm), C.byref(vp), C.byref(nv), C.byref(done))
     if vp.value:
         lib.og_free(vp)
     del keep
@@ -194,11 +206,12 @@ def sort_tuples(t: np.ndarray) -> np.ndarray:
     return t[np.lexsort(t.T[::-1])]
 
 
-def validate(graph_or_og, gfd, roots=None, threads: int = 1, lib=None):
-    """(n_matches, sorted violations [n, k]) of one GFD; see module docstring."""
+def validate(graph_or_og, gfd, roots=None, threads: int = 1, lib=None, induced: bool = True):
+    """(n_matches, sorted violations [n, k]) of one GFD; see module docstring.
+    induced=False selects the non-induced mode (only Q's edges constrain h)."""
     og = graph_or_og if isinstance(graph_or_og, OracleGraph) else OracleGraph(graph_or_og, lib)
     if threads <= 1:
-        nm, v = _run(og, gfd, roots)
+        nm, v = _run(og, gfd, roots, induced)
         return nm, sort_tuples(v)
     if roots is None:
         roots = np.arange(og.n, dtype=np.int32)
@@ -206,7 +219,7 @@ def validate(graph_or_og, gfd, roots=None, threads: int = 1, lib=None):
     # interleaved slices spread hubs over the threads
     parts = [roots[i::threads * 8] for i in range(threads * 8)]
     with ThreadPoolExecutor(threads) as ex:
-        res = list(ex.map(lambda r: _run(og, gfd, r), parts))
+        res = list(ex.map(lambda r: _run(og, gfd, r, induced), parts))
     nm = sum(r[0] for r in res)
     v = np.concatenate([r[1] for r in res]) if res else np.zeros((0, gfd.k), np.int32)
     return nm, sort_tuples(v)

@@ -35,6 +35,10 @@ MUTANTS = {
     "var_literal_wrong_attr": ("vb = og_attr(s->g, l->b, s->h[l->y]);",
                                "vb = og_attr(s->g, l->a, s->h[l->y]);"),
     "vertex_label_ignored": ("if (!og_label_ok(s->q->node_label[u], g->vlabel[v])) return 0;", ""),
+    # non-induced mode
+    "non_induced_mode_still_induced": ("if (!og_induced && ql == OG_NOEDGE) return 1;", ""),
+    "non_induced_mode_drops_required_edges": ("if (!og_induced && ql == OG_NOEDGE) return 1;",
+                                              "if (!og_induced) return 1;"),
 }
 
 
@@ -59,6 +63,15 @@ def _pins_pass(lib) -> bool:
         nm, v = run(g, q)
         if nm != n_matches or not np.array_equal(v, viol):
             return False
+    # the non-induced mode's pins
+    for seed in range(80):
+        g, q = random_case(seed)
+        nm, v = O.validate(g, q, lib=lib, induced=False)
+        bnm, bv = brute_force(g, q, induced=False)
+        if nm != bnm or not np.array_equal(v, bv):
+            return False
+    if O.validate(complete_bidirected(5), undirected_q(3, [(0, 1), (1, 2)]), lib=lib, induced=False)[0] != 60:
+        return False
     return True
 
 
