@@ -235,13 +235,14 @@ def main():
     ap.add_argument("--scale", type=int, default=1, help="divide V and E (tests only)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-non-induced", action="store_true", help="skip the non-induced matching leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flags", type=int, default=0)
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="frontier budget in GiB (0: the library default)")
     ap.add_argument("--hint", type=int, default=1 << 26,
                     help="violation records stored per call before a re-run")
-    ap.add_argument("--serve-rates", default="200,1000,2000",
+    ap.add_argument("--serve-rates", default="50,200,500,1000,2000",
                     help="Poisson arrival rates (req/s) of the serving leg; empty: skip")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--n-gfds", type=int, default=0, help="validate only the first N GFDs (profiling)")
@@ -387,6 +388,34 @@ def main():
         plain = {"value": pm / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms,
                  "launch": f"{len(qs)} gfd_validate calls per step"}
 
+    # the non-induced matching mode (GFD_FLAG_NON_INDUCED) on the same batch:
+    # a different result (supersets of the matches and violations), reported
+    # beside the headline, never in place of it
+    non_induced = None
+    if not args.no_non_induced:
+        nflags = flags | G.FLAG_NON_INDUCED
+        res = dg.validate_batch(qs, stream=stream, flags=nflags, max_violations_hint=hint,
+                                frontier_budget_bytes=budget, kernel_variant=args.kernel_variant)
+        ntimes, nenum = [], []
+        for _ in range(max(1, min(2, args.steps))):
+            l2_flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = dg.validate_batch(qs, stream=stream, flags=nflags, max_violations_hint=hint,
+                                    frontier_budget_bytes=budget, kernel_variant=args.kernel_variant)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ntimes.append(e0.elapsed_time(e1))
+            nenum.append(res[0].profile(G.PROF_ENUM)[0])
+        nm = sum(r.n_matches for r in res)
+        nms = float(np.mean(ntimes))
+        non_induced = {"value": nm / (nms / 1000.0), "unit": UNIT, "ms_per_step": nms,
+                       "enum_ms": float(np.mean(nenum)), "matches_per_step": nm,
+                       "violations_per_step": sum(r.n_violations for r in res),
+                       "work_items_per_step": sum(r.stat(G.STAT_WORK) for r in res)}
+
     # serving: a Poisson stream of single-GFD requests against the resident
     # graph, continuous batching vs one gfd_validate per request
     serving = None
@@ -424,7 +453,7 @@ def main():
                                                   "every timed step",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "plain": plain, "serving": serving, "autotuned": tuned,
+                "clocks": clk, "plain": plain, "non_induced": non_induced, "serving": serving, "autotuned": tuned,
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,
                 "matches_per_step": matches, "violations_per_step": viols,
                 "work_items_per_step": work, "edge_probes_per_step": probes,

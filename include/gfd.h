@@ -127,6 +127,15 @@ typedef struct {
 #define GFD_FLAG_PROFILE       0x4  /* time each kernel class with CUDA events;
                                        read back with gfd_result_profile() */
 #define GFD_FLAG_NO_GRAPH      0x8  /* host loop without CUDA-graph capture */
+#define GFD_FLAG_NON_INDUCED   0x10 /* non-induced matching: only the pairs in E_Q
+                                       constrain a match ((a,b) in E_Q implies
+                                       (h(a),h(b)) in E with an agreeing label);
+                                       pairs outside E_Q, self-pairs included, are
+                                       free. The matching of Bi et al. that
+                                       Section III contrasts with the paper's
+                                       (induced) definition, and the reading of
+                                       the path query of Section V. Changes the
+                                       result: matches and Vio are supersets. */
 
 /* Tuning options; a NULL gfd_opts* or zero fields select the defaults. */
 typedef struct {

@@ -66,7 +66,7 @@ struct FilterKey {
     int32_t label;     // or GFD_WILDCARD
     uint32_t dout_min;
     uint32_t din_min;
-    int32_t self_exp;  // EXP_NONE, EXP_ANY or a label
+    int32_t self_exp;  // EXP_NONE, EXP_ANY, a label, or EXP_SKIP (no condition)
 };
 
 struct LevelPlan {

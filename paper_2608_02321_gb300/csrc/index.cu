@@ -56,7 +56,8 @@ __global__ void k_filter(DevGraph g, const FilterKey* __restrict__ keys, int nke
         din -= has_self;
         for (int k = 0; k < nkeys; k++) {
             const FilterKey key = sk[k];
-            bool self_ok = key.self_exp == EXP_NONE ? !has_self
+            bool self_ok = key.self_exp == EXP_SKIP ? true
+                         : key.self_exp == EXP_NONE ? !has_self
                          : key.self_exp == EXP_ANY  ? has_self
                                                     : (has_self && self_lab == key.self_exp);
             bool p = valid && label_ok(key.label, L) && dout >= key.dout_min && din >= key.din_min && self_ok;

@@ -33,7 +33,7 @@ int32_t exp_of(int32_t qlab) { return qlab == NOEDGE ? EXP_NONE : qlab; }
 
 }  // namespace
 
-int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostPlan* P) {
+int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostPlan* P, bool induced) {
     if (!phi) {
         set_error(GFD_ERR_INVALID_ARG, "NULL GFD");
         return GFD_ERR_INVALID_ARG;
@@ -252,13 +252,14 @@ int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostP
             if (lu == GFD_WILDCARD || lw == GFD_WILDCARD || lu == lw) L.inj |= 1u << h;
             const bool skip_out = h == L.par && L.tdir == 0;  // u -> parent is the tree edge
             const bool skip_in = h == L.par && L.tdir == 1;   // parent -> u is the tree edge
-            if (!skip_out) {
+            // non-induced matching checks only the pairs that are edges of Q
+            if (!skip_out && (induced || q[u][w] != NOEDGE)) {
                 L.chk_q[n] = (int8_t)h;
                 L.chk_dir[n] = 1;
                 L.chk_exp[n] = (int16_t)exp_of(q[u][w]);
                 n++;
             }
-            if (!skip_in) {
+            if (!skip_in && (induced || q[w][u] != NOEDGE)) {
                 L.chk_q[n] = (int8_t)h;
                 L.chk_dir[n] = 0;
                 L.chk_exp[n] = (int16_t)exp_of(q[w][u]);
@@ -303,7 +304,7 @@ int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostP
             K.dout_min += q[u][w] != NOEDGE;
             K.din_min += q[w][u] != NOEDGE;
         }
-        K.self_exp = exp_of(q[u][u]);
+        K.self_exp = !induced && q[u][u] == NOEDGE ? EXP_SKIP : exp_of(q[u][u]);
         // refinement constraints
         P->td[i].clear();
         P->bu[i].clear();

@@ -45,7 +45,9 @@ struct PlanStats {
     const double* elabel_frac = nullptr;  // [256]
 };
 
-// Returns GFD_OK or an error code (message set).
-int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostPlan* out);
+// Returns GFD_OK or an error code (message set). induced = false plans the
+// non-induced matching: no absent-edge checks and no self-loop requirement on
+// pattern nodes without one.
+int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostPlan* out, bool induced = true);
 
 }  // namespace gfd

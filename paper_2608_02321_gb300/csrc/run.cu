@@ -258,7 +258,9 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
     G->n = n;
     G->plans.resize(n);
     for (int s = 0; s < n; s++)
-        if (int rc = make_plan(phis[s], g->n_attrs, g->plan_stats(), &G->plans[s])) return rc;
+        if (int rc = make_plan(phis[s], g->n_attrs, g->plan_stats(), &G->plans[s],
+                               !(o && (o->flags & GFD_FLAG_NON_INDUCED))))
+            return rc;
     std::map<std::tuple<int32_t, uint32_t, uint32_t, int32_t>, int> key_id;
     G->slot_key.resize(n);
     for (int s = 0; s < n; s++)
@@ -931,7 +933,8 @@ int session_submit(gfd_session* S, const gfd_gfd* phi, int64_t* id) {
     }
     // plan now so that an invalid GFD is reported at submission
     HostPlan P;
-    if (int rc = make_plan(phi, S->g->n_attrs, S->g->plan_stats(), &P)) return rc;
+    if (int rc = make_plan(phi, S->g->n_attrs, S->g->plan_stats(), &P, !(S->opts.flags & GFD_FLAG_NON_INDUCED)))
+        return rc;
     auto R = std::make_unique<Request>();
     R->id = S->next_id++;
     R->node_label.assign(phi->node_label, phi->node_label + phi->k);
