@@ -33,8 +33,9 @@ def _holds(lit, h, attrs):
     return vb != ABSENT and va == vb
 
 
-def brute_force(graph, gfd, induced: bool = True):
-    """(n_matches, sorted violations [n, k])."""
+def brute_force(graph, gfd, induced: bool = True, count: str = "all"):
+    """(n_matches, sorted violations [n, k]); count="x" counts only the matches
+    whose X literals all hold."""
     E = _edge_map(graph)
     k = gfd.k
     qe = {(a, b): l for (a, b, l) in gfd.edges}
@@ -62,8 +63,9 @@ def brute_force(graph, gfd, induced: bool = True):
                 break
         if not ok:
             continue
-        n_matches += 1
-        if not all(_holds(l, h, attrs) for l in gfd.X):
+        x_ok = all(_holds(l, h, attrs) for l in gfd.X)
+        n_matches += 1 if (count == "all" or x_ok) else 0
+        if not x_ok:
             continue
         if gfd.y_false or not all(_holds(l, h, attrs) for l in gfd.Y):
             viol.append(h)

@@ -164,6 +164,7 @@ typedef struct {
     int32_t pout[OG_MAXK];             /* 1: iterate out-nbrs of h(pnode), 0: in-nbrs */
     int32_t h[OG_MAXK];                /* h[node] = vertex */
     uint64_t n_matches;
+    uint64_t n_x_matches;              /* matches with h ⊨ X */
     int32_t *viol; int64_t n_viol, cap_viol;
     double deadline;                   /* monotonic seconds; 0 = none */
     uint64_t calls;
@@ -213,6 +214,7 @@ static void og_record(og_state *s) {
     s->n_matches++;
     for (i = 0; i < q->nx; i++) x_ok = x_ok && og_lit_holds(s, &q->X[i]);
     if (!x_ok) return;
+    s->n_x_matches++;
     if (q->y_false) y_ok = 0;
     else for (i = 0; i < q->ny; i++) y_ok = y_ok && og_lit_holds(s, &q->Y[i]);
     if (y_ok) return;
@@ -264,7 +266,8 @@ static void og_extend(og_state *s, int i) {
 }
 
 /* Validate one GFD; induced = 1 is the paper's matching, 0 the non-induced
- * mode described at the top. roots: the vertices tried for pattern node 0 (NULL: all of V).
+ * mode described at the top. *n_x_matches (if not NULL) receives the number of
+ * matches that satisfy X (Section II: only they can be violations). roots: the vertices tried for pattern node 0 (NULL: all of V).
  * seconds > 0 bounds the run: the root being searched when time runs out is
  * dropped together with its matches, and *roots_done tells how many roots were
  * searched to the end (all of them when there is no bound).
@@ -272,7 +275,7 @@ static void og_extend(og_state *s, int i) {
  * caller owns *viol_out (free with og_free). */
 int og_validate_mode(const og_graph *g, const og_gfd *q, int induced, const int32_t *roots, int64_t n_roots,
                      double seconds, uint64_t *n_matches, int32_t **viol_out, int64_t *n_viol,
-                     int64_t *roots_done) {
+                     int64_t *roots_done, uint64_t *n_x_matches) {
     og_state s;
     int32_t placed[OG_MAXK];
     int i, j, head, tail;
@@ -320,7 +323,7 @@ int og_validate_mode(const og_graph *g, const og_gfd *q, int induced, const int3
     s.deadline = seconds > 0 ? og_now() + seconds : 0;
     for (r = 0; r < (roots ? n_roots : (int64_t)g->n); r++) {
         int32_t v = roots ? roots[r] : (int32_t)r;
-        uint64_t m0 = s.n_matches;
+        uint64_t m0 = s.n_matches, x0 = s.n_x_matches;
         int64_t v0 = s.n_viol;
         if (v < 0 || v >= g->n) continue;
         if (!og_candidate_ok(&s, 0, v)) continue;
@@ -328,12 +331,14 @@ int og_validate_mode(const og_graph *g, const og_gfd *q, int induced, const int3
         og_extend(&s, 1);
         if (s.aborted) {          /* drop the unfinished root */
             s.n_matches = m0;
+            s.n_x_matches = x0;
             s.n_viol = v0;
             break;
         }
     }
     if (roots_done) *roots_done = r;
     *n_matches = s.n_matches;
+    if (n_x_matches) *n_x_matches = s.n_x_matches;
     *viol_out = s.viol;
     *n_viol = s.n_viol;
     return 0;
@@ -343,12 +348,12 @@ int og_validate_mode(const og_graph *g, const og_gfd *q, int induced, const int3
 int og_validate_budget(const og_graph *g, const og_gfd *q, const int32_t *roots, int64_t n_roots,
                        double seconds, uint64_t *n_matches, int32_t **viol_out, int64_t *n_viol,
                        int64_t *roots_done) {
-    return og_validate_mode(g, q, 1, roots, n_roots, seconds, n_matches, viol_out, n_viol, roots_done);
+    return og_validate_mode(g, q, 1, roots, n_roots, seconds, n_matches, viol_out, n_viol, roots_done, NULL);
 }
 
 int og_validate(const og_graph *g, const og_gfd *q, const int32_t *roots, int64_t n_roots,
                 uint64_t *n_matches, int32_t **viol_out, int64_t *n_viol) {
-    return og_validate_mode(g, q, 1, roots, n_roots, 0.0, n_matches, viol_out, n_viol, NULL);
+    return og_validate_mode(g, q, 1, roots, n_roots, 0.0, n_matches, viol_out, n_viol, NULL, NULL);
 }
 
 /* --------------------------------------------------------------- sorting */

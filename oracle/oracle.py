@@ -67,7 +67,7 @@ def bind_library(path: str):
     lib.og_validate_mode.restype = C.c_int
     lib.og_validate_mode.argtypes = [C.c_void_p, C.POINTER(_Gfd), C.c_int, C.c_void_p, C.c_int64, C.c_double,
                                      C.POINTER(C.c_uint64), C.POINTER(C.c_void_p),
-                                     C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+                                     C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_uint64)]
     lib.og_free.argtypes = [C.c_void_p]
     return lib
 
@@ -144,26 +144,28 @@ def _gfd_struct(gfd):
     return s, keep
 
 
-def _run(og: OracleGraph, gfd, roots, induced: bool = True):
+def _run(og: OracleGraph, gfd, roots, induced: bool = True, count: str = "all"):
     lib = og._lib
     s, keep = _gfd_struct(gfd)
     nm = C.c_uint64(0)
+    nx = C.c_uint64(0)
     vp = C.c_void_p(None)
     nv = C.c_int64(0)
-    if roots is None:
-        if induced:
-            rc = lib.og_validate(og._h, C.byref(s), None, 0, C.byref(nm), C.byref(vp), C.byref(nv))
-        else:
-            rc = lib.og_validate_mode(og._h, C.byref(s), 0, None, 0, 0.0, C.byref(nm), C.byref(vp),
-                                      C.byref(nv), None)
+    if roots is None and induced and count == "all":
+        rc = lib.og_validate(og._h, C.byref(s), None, 0, C.byref(nm), C.byref(vp), C.byref(nv))
+    elif roots is None:
+        rc = lib.og_validate_mode(og._h, C.byref(s), 1 if induced else 0, None, 0, 0.0, C.byref(nm),
+                                  C.byref(vp), C.byref(nv), None, C.byref(nx))
     else:
         r = np.ascontiguousarray(roots, dtype=np.int32)
-        if induced:
+        if induced and count == "all":
             rc = lib.og_validate(og._h, C.byref(s), _ptr(r), int(r.shape[0]), C.byref(nm),
                                  C.byref(vp), C.byref(nv))
         else:
-            rc = lib.og_validate_mode(og._h, C.byref(s), 0, _ptr(r), int(r.shape[0]), 0.0, C.byref(nm),
-                                      C.byref(vp), C.byref(nv), None)
+            rc = lib.og_validate_mode(og._h, C.byref(s), 1 if induced else 0, _ptr(r), int(r.shape[0]), 0.0,
+                                      C.byref(nm), C.byref(vp), C.byref(nv), None, C.byref(nx))
+    if count == "x":
+        nm = nx
     if rc != 0:
         raise ValueError("oracle rejected the GFD (malformed or disconnected pattern)")
     k = gfd.k
@@ -190,7 +192,7 @@ def count_within(og: OracleGraph, gfd, roots, seconds: float, induced: bool = Tr
     done = C.c_int64(0)
     r = np.ascontiguousarray(roots, dtype=np.int32)
     rc = lib.og_validate_mode(og._h, C.byref(s), 1 if induced else 0, _ptr(r), int(r.shape[0]),
-                              float(seconds), C.byref(nm), C.byref(vp), C.byref(nv), C.byref(done))
+                              float(seconds), C.byref(nm), C.byref(vp), C.byref(nv), C.byref(done), None)
     if vp.value:
         lib.og_free(vp)
     del keep
@@ -206,12 +208,15 @@ def sort_tuples(t: np.ndarray) -> np.ndarray:
     return t[np.lexsort(t.T[::-1])]
 
 
-def validate(graph_or_og, gfd, roots=None, threads: int = 1, lib=None, induced: bool = True):
+def validate(graph_or_og, gfd, roots=None, threads: int = 1, lib=None, induced: bool = True,
+             count: str = "all"):
     """(n_matches, sorted violations [n, k]) of one GFD; see module docstring.
-    induced=False selects the non-induced mode (only Q's edges constrain h)."""
+    induced=False selects the non-induced mode (only Q's edges constrain h);
+    count="x" counts only the matches that satisfy X (the violations are the
+    same either way)."""
     og = graph_or_og if isinstance(graph_or_og, OracleGraph) else OracleGraph(graph_or_og, lib)
     if threads <= 1:
-        nm, v = _run(og, gfd, roots, induced)
+        nm, v = _run(og, gfd, roots, induced, count)
         return nm, sort_tuples(v)
     if roots is None:
         roots = np.arange(og.n, dtype=np.int32)
@@ -219,7 +224,7 @@ def validate(graph_or_og, gfd, roots=None, threads: int = 1, lib=None, induced: 
     # interleaved slices spread hubs over the threads
     parts = [roots[i::threads * 8] for i in range(threads * 8)]
     with ThreadPoolExecutor(threads) as ex:
-        res = list(ex.map(lambda r: _run(og, gfd, r, induced), parts))
+        res = list(ex.map(lambda r: _run(og, gfd, r, induced, count), parts))
     nm = sum(r[0] for r in res)
     v = np.concatenate([r[1] for r in res]) if res else np.zeros((0, gfd.k), np.int32)
     return nm, sort_tuples(v)

@@ -39,6 +39,9 @@ MUTANTS = {
     "non_induced_mode_still_induced": ("if (!og_induced && ql == OG_NOEDGE) return 1;", ""),
     "non_induced_mode_drops_required_edges": ("if (!og_induced && ql == OG_NOEDGE) return 1;",
                                               "if (!og_induced) return 1;"),
+    # count of X-satisfying matches
+    "x_count_ignores_x": ("    if (!x_ok) return;\n    s->n_x_matches++;",
+                          "    s->n_x_matches++;\n    if (!x_ok) return;"),
 }
 
 
@@ -72,6 +75,13 @@ def _pins_pass(lib) -> bool:
             return False
     if O.validate(complete_bidirected(5), undirected_q(3, [(0, 1), (1, 2)]), lib=lib, induced=False)[0] != 60:
         return False
+    # the count of X-satisfying matches
+    for seed in range(80):
+        g, q = random_case(seed)
+        nx, v = O.validate(g, q, lib=lib, count="x")
+        bnx, bv = brute_force(g, q, count="x")
+        if nx != bnx or not np.array_equal(v, bv):
+            return False
     return True
 
 
