@@ -213,8 +213,8 @@ static void og_record(og_state *s) {
     int i, x_ok = 1, y_ok = 1;
     s->n_matches++;
     for (i = 0; i < q->nx; i++) x_ok = x_ok && og_lit_holds(s, &q->X[i]);
+    s->n_x_matches += (uint64_t)x_ok;
     if (!x_ok) return;
-    s->n_x_matches++;
     if (q->y_false) y_ok = 0;
     else for (i = 0; i < q->ny; i++) y_ok = y_ok && og_lit_holds(s, &q->Y[i]);
     if (y_ok) return;
