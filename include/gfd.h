@@ -136,6 +136,13 @@ typedef struct {
                                        (induced) definition, and the reading of
                                        the path query of Section V. Changes the
                                        result: matches and Vio are supersets. */
+#define GFD_FLAG_PUSH_X        0x20 /* apply X during the search: constant X
+                                       literals in the candidate filter (two per
+                                       pattern node), the others as soon as both
+                                       ends are matched. Only matches satisfying
+                                       X can be violations (Section II), so Vio is
+                                       unchanged; gfd_result_matches then counts
+                                       the matches that satisfy X. */
 
 /* Tuning options; a NULL gfd_opts* or zero fields select the defaults. */
 typedef struct {

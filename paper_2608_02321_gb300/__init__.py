@@ -32,6 +32,7 @@ FLAG_HOST_LOOP = 0x2
 FLAG_PROFILE = 0x4
 FLAG_NO_GRAPH = 0x8
 FLAG_NON_INDUCED = 0x10
+FLAG_PUSH_X = 0x20
 
 PROF_FILTER, PROF_REFINE, PROF_INDEX, PROF_ENUM, PROF_SORT = range(5)
 STAT_STEPS, STAT_WORK, STAT_ROWS, STAT_PROBES, STAT_CANDIDATES, STAT_INDEX, STAT_RERUN = range(7)

@@ -62,11 +62,16 @@ __host__ __device__ __forceinline__ uint32_t sig_bit(uint32_t v) { return (v * 0
 
 // Candidate filter key (Section III.B step 1a-1b): label, degree lower bounds
 // (self-loops excluded on both sides) and the self-loop expectation.
+constexpr int KEY_ATTRS = 2;  // constant X literals a filter key can carry
+
 struct FilterKey {
     int32_t label;     // or GFD_WILDCARD
     uint32_t dout_min;
     uint32_t din_min;
     int32_t self_exp;  // EXP_NONE, EXP_ANY, a label, or EXP_SKIP (no condition)
+    int32_t n_attr;    // attribute conditions attr[a] = c (pushed-down constant X literals)
+    int32_t attr_a[KEY_ATTRS];
+    int32_t attr_c[KEY_ATTRS];
 };
 
 struct LevelPlan {
@@ -91,12 +96,14 @@ struct DevLit {
     int32_t yl;    // level of y
     int32_t b;
     int32_t c;
+    int32_t lvl;   // level whose candidates are checked against it (-1: in the filter)
 };
 
 // Everything the device needs about one GFD slot.
 struct SlotDesc {
     int32_t k;
     int32_t nx, ny, y_false;
+    int32_t push_x;  // X applied during the search: count only matches with h |= X
     int32_t order[MAXK];
     LevelPlan lv[MAXK];
     DevLit lit[MAXLIT];  // X literals then Y literals

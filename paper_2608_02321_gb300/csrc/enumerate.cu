@@ -322,14 +322,21 @@ __device__ void expand_warps(const EnumArgs& A) {
                     }
                 }
                 m[i] = v;
+                // X pushed down: the X literals whose ends are matched at this
+                // level (before the last one; the last level checks its own below)
+                if (ok && D->push_x && !last)
+                    for (int q = 0; q < D->nx && ok; q++)
+                        if (D->lit[q].lvl == i) ok = lit_holds(g, D->lit[q], m);
             }
             if (last) {
-                // complete match: count it, check X -> Y, emit a violation
+                // complete match: check the X literals of this level, count it
+                // (with X pushed down only if they hold), check Y, emit a violation
                 bool viol = false;
                 if (ok) {
-                    tile_matches++;
                     bool x_ok = true;
-                    for (int q = 0; q < D->nx && x_ok; q++) x_ok = lit_holds(g, D->lit[q], m);
+                    for (int q = 0; q < D->nx && x_ok; q++)
+                        if (D->lit[q].lvl == i) x_ok = lit_holds(g, D->lit[q], m);
+                    tile_matches += x_ok || !D->push_x;
                     if (x_ok) {
                         bool y_ok = !D->y_false;
                         for (int q = 0; q < D->ny && y_ok; q++) y_ok = lit_holds(g, D->lit[D->nx + q], m);

@@ -61,6 +61,10 @@ __global__ void k_filter(DevGraph g, const FilterKey* __restrict__ keys, int nke
                          : key.self_exp == EXP_ANY  ? has_self
                                                     : (has_self && self_lab == key.self_exp);
             bool p = valid && label_ok(key.label, L) && dout >= key.dout_min && din >= key.din_min && self_ok;
+            for (int t = 0; t < key.n_attr; t++) {  // pushed-down constant X literals
+                const int32_t va = p ? g.attrs[(uint64_t)key.attr_a[t] * g.n + v] : GFD_ATTR_ABSENT;
+                p = p && va != GFD_ATTR_ABSENT && va == key.attr_c[t];
+            }
             uint32_t b = __ballot_sync(0xffffffffu, p);
             if (lane == 0) out[(uint64_t)k * g.nwords + w] = b;
         }
@@ -479,12 +483,20 @@ int check_launch(const char* what) {
 int launch_filter(const DevGraph& g, const FilterKey* d_keys, int nkeys, uint32_t* d_out, cudaStream_t st) {
     if (nkeys <= 0 || g.nwords == 0) return GFD_OK;
     int blocks = (int)std::min<uint64_t>((g.nwords * 32 + FILTER_THREADS - 1) / FILTER_THREADS, 152 * 8);
-    size_t smem = sizeof(FilterKey) * nkeys;
-    if (smem > 48 * 1024) {
-        cudaFuncSetAttribute(k_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // keys staged in shared memory: at most KEYS_PER_LAUNCH per launch
+    constexpr int KEYS_PER_LAUNCH = 4096;
+    for (int k0 = 0; k0 < nkeys; k0 += KEYS_PER_LAUNCH) {
+        const int cnt = std::min(KEYS_PER_LAUNCH, nkeys - k0);
+        const size_t smem = sizeof(FilterKey) * cnt;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_filter)");
+        }
+        k_filter<<<std::max(blocks, 1), FILTER_THREADS, smem, st>>>(g, d_keys + k0, cnt,
+                                                                    d_out + (uint64_t)k0 * g.nwords);
+        if (int rc = check_launch("k_filter")) return rc;
     }
-    k_filter<<<std::max(blocks, 1), FILTER_THREADS, smem, st>>>(g, d_keys, nkeys, d_out);
-    return check_launch("k_filter");
+    return GFD_OK;
 }
 
 int launch_and(const DevGraph& g, const AndJob* d_jobs, int njobs, cudaStream_t st) {

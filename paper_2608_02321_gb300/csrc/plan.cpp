@@ -33,7 +33,8 @@ int32_t exp_of(int32_t qlab) { return qlab == NOEDGE ? EXP_NONE : qlab; }
 
 }  // namespace
 
-int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostPlan* P, bool induced) {
+int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostPlan* P, bool induced,
+              bool push_x) {
     if (!phi) {
         set_error(GFD_ERR_INVALID_ARG, "NULL GFD");
         return GFD_ERR_INVALID_ARG;
@@ -305,6 +306,8 @@ int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostP
             K.din_min += q[w][u] != NOEDGE;
         }
         K.self_exp = !induced && q[u][u] == NOEDGE ? EXP_SKIP : exp_of(q[u][u]);
+        K.n_attr = 0;
+        for (int t = 0; t < KEY_ATTRS; t++) K.attr_a[t] = K.attr_c[t] = 0;
         // refinement constraints
         P->td[i].clear();
         P->bu[i].clear();
@@ -315,9 +318,11 @@ int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostP
             if (q[w][u] != NOEDGE) (h < i ? P->td[i] : P->bu[i]).push_back(Con{(int8_t)h, 0, q[w][u]});
         }
     }
-    // literals
+    // literals: checked at the last level, or with X pushed down at the level
+    // where both ends are matched (constants in that node's filter key)
     P->lits.clear();
-    auto add_lit = [&](const gfd_literal& l) -> int {
+    P->push_x = push_x;
+    auto add_lit = [&](const gfd_literal& l, bool is_x) -> int {
         if ((l.kind != 0 && l.kind != 1) || l.x < 0 || l.x >= k || l.a < 0 || l.a >= n_attrs ||
             (l.kind == 1 && (l.y < 0 || l.y >= k || l.b < 0 || l.b >= n_attrs))) {
             set_error(GFD_ERR_INVALID_ARG, "literal refers to a missing node or attribute");
@@ -330,18 +335,41 @@ int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostP
         d.yl = l.kind == 1 ? P->level_of[l.y] : 0;
         d.b = l.kind == 1 ? l.b : 0;
         d.c = l.c;
+        d.lvl = k - 1;
+        if (is_x && push_x) {
+            FilterKey& K = P->key[d.xl];
+            if (l.kind == 0 && K.n_attr < KEY_ATTRS) {
+                K.attr_a[K.n_attr] = l.a;
+                K.attr_c[K.n_attr] = l.c;
+                K.n_attr++;
+                d.lvl = -1;
+            } else {
+                d.lvl = l.kind == 1 ? std::max(d.xl, d.yl) : d.xl;
+                // level 0 is never expanded (its candidates are the roots): a
+                // literal on the root alone is checked with level 1
+                if (k > 1 && d.lvl == 0) d.lvl = 1;
+            }
+        }
         P->lits.push_back(d);
         return GFD_OK;
     };
     for (int i = 0; i < phi->nx; i++)
-        if (int rc = add_lit(phi->X[i])) return rc;
+        if (int rc = add_lit(phi->X[i], true)) return rc;
     P->nx = phi->nx;
     P->y_false = phi->y_false ? 1 : 0;
     P->ny = 0;
     if (!P->y_false) {
         for (int i = 0; i < phi->ny; i++)
-            if (int rc = add_lit(phi->Y[i])) return rc;
+            if (int rc = add_lit(phi->Y[i], false)) return rc;
         P->ny = phi->ny;
+    }
+    // a canonical order of the filter conditions, so equal keys are shared
+    for (int i = 0; i < k; i++) {
+        FilterKey& K = P->key[i];
+        if (K.n_attr == 2 && (K.attr_a[1] < K.attr_a[0] || (K.attr_a[1] == K.attr_a[0] && K.attr_c[1] < K.attr_c[0]))) {
+            std::swap(K.attr_a[0], K.attr_a[1]);
+            std::swap(K.attr_c[0], K.attr_c[1]);
+        }
     }
     return GFD_OK;
 }

@@ -31,6 +31,7 @@ struct HostPlan {
     std::vector<Con> bu[MAXK];  // constraints from later levels
     std::vector<DevLit> lits;   // X then Y
     int nx = 0, ny = 0, y_false = 0;
+    bool push_x = false;
 };
 
 // Graph statistics used to order the pattern: per vertex label L the moments
@@ -48,6 +49,10 @@ struct PlanStats {
 // Returns GFD_OK or an error code (message set). induced = false plans the
 // non-induced matching: no absent-edge checks and no self-loop requirement on
 // pattern nodes without one.
-int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostPlan* out, bool induced = true);
+// push_x = true places each X literal at the level where both its ends are
+// matched and moves constant ones into the candidate filter (up to KEY_ATTRS
+// per pattern node).
+int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostPlan* out, bool induced = true,
+              bool push_x = false);
 
 }  // namespace gfd

@@ -259,14 +259,18 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
     G->plans.resize(n);
     for (int s = 0; s < n; s++)
         if (int rc = make_plan(phis[s], g->n_attrs, g->plan_stats(), &G->plans[s],
-                               !(o && (o->flags & GFD_FLAG_NON_INDUCED))))
+                               !(o && (o->flags & GFD_FLAG_NON_INDUCED)), o && (o->flags & GFD_FLAG_PUSH_X)))
             return rc;
-    std::map<std::tuple<int32_t, uint32_t, uint32_t, int32_t>, int> key_id;
+    std::map<std::vector<int64_t>, int> key_id;
     G->slot_key.resize(n);
     for (int s = 0; s < n; s++)
         for (int i = 0; i < G->plans[s].k; i++) {
             const FilterKey& K = G->plans[s].key[i];
-            auto t = std::make_tuple(K.label, K.dout_min, K.din_min, K.self_exp);
+            std::vector<int64_t> t = {K.label, K.dout_min, K.din_min, K.self_exp, K.n_attr};
+            for (int a = 0; a < K.n_attr; a++) {
+                t.push_back(K.attr_a[a]);
+                t.push_back(K.attr_c[a]);
+            }
             auto it = key_id.find(t);
             if (it == key_id.end()) {
                 it = key_id.emplace(t, (int)G->keys.size()).first;
@@ -300,6 +304,7 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
         D.nx = P.nx;
         D.ny = P.ny;
         D.y_false = P.y_false;
+        D.push_x = P.push_x ? 1 : 0;
         for (int i = 0; i < P.k; i++) {
             D.order[i] = P.order[i];
             D.lv[i] = P.lv[i];
@@ -933,7 +938,8 @@ int session_submit(gfd_session* S, const gfd_gfd* phi, int64_t* id) {
     }
     // plan now so that an invalid GFD is reported at submission
     HostPlan P;
-    if (int rc = make_plan(phi, S->g->n_attrs, S->g->plan_stats(), &P, !(S->opts.flags & GFD_FLAG_NON_INDUCED)))
+    if (int rc = make_plan(phi, S->g->n_attrs, S->g->plan_stats(), &P, !(S->opts.flags & GFD_FLAG_NON_INDUCED),
+                           (S->opts.flags & GFD_FLAG_PUSH_X) != 0))
         return rc;
     auto R = std::make_unique<Request>();
     R->id = S->next_id++;
