@@ -29,9 +29,13 @@
  *
  * Algorithm: Ullmann-style backtracking (Section III's description of the
  * generic scheme). Node 0 first, then breadth-first over the undirected
- * skeleton of Q visiting neighbours by increasing node id. Level 0 tries every
- * vertex of G (or a caller-given subset of them); level i tries the out- or
- * in-neighbours of the image of the first already-placed skeleton neighbour.
+ * skeleton of Q visiting neighbours by increasing node id; a disconnected
+ * pattern continues with the lowest unplaced node of the next component. Level
+ * 0 tries every vertex of G (or a caller-given subset of them); level i tries
+ * the out- or in-neighbours of the image of the first already-placed skeleton
+ * neighbour, or every vertex of G when it starts a new component (the match
+ * conditions are the same for pairs across components: injective, and in the
+ * induced mode no G edge where Q has none).
  * Every candidate is checked against ALL conditions above versus ALL nodes
  * placed before it. Edge lookup is a binary search in the oracle's own sorted
  * copy of the adjacency.
@@ -249,11 +253,14 @@ static void og_extend(og_state *s, int i) {
     int64_t e, a, b;
     if (i == s->q->k) { og_record(s); return; }
     u = s->order[i];
-    hp = s->h[s->pnode[i]];
-    if (s->pout[i]) { a = g->out_off[hp]; b = g->out_off[hp + 1]; }
-    else            { a = g->in_off[hp];  b = g->in_off[hp + 1]; }
+    if (s->pnode[i] < 0) { a = 0; b = g->n; hp = -1; }           /* every vertex */
+    else {
+        hp = s->h[s->pnode[i]];
+        if (s->pout[i]) { a = g->out_off[hp]; b = g->out_off[hp + 1]; }
+        else            { a = g->in_off[hp];  b = g->in_off[hp + 1]; }
+    }
     for (e = a; e < b; e++) {
-        int32_t v = s->pout[i] ? g->out_nbr[e] : g->in_nbr[e];
+        int32_t v = hp < 0 ? (int32_t)e : s->pout[i] ? g->out_nbr[e] : g->in_nbr[e];
         if (s->aborted) return;
         if (s->deadline > 0 && (++s->calls & 0xfff) == 0 && og_now() > s->deadline) {
             s->aborted = 1;
@@ -271,7 +278,7 @@ static void og_extend(og_state *s, int i) {
  * seconds > 0 bounds the run: the root being searched when time runs out is
  * dropped together with its matches, and *roots_done tells how many roots were
  * searched to the end (all of them when there is no bound).
- * Returns 0 on success, 1 for a malformed or disconnected pattern. On success the
+ * Returns 0 on success, 1 for a malformed pattern. On success the
  * caller owns *viol_out (free with og_free). */
 int og_validate_mode(const og_graph *g, const og_gfd *q, int induced, const int32_t *roots, int64_t n_roots,
                      double seconds, uint64_t *n_matches, int32_t **viol_out, int64_t *n_viol,
@@ -299,21 +306,28 @@ int og_validate_mode(const og_graph *g, const og_gfd *q, int induced, const int3
             return 1;
         if (l->kind != 0 && l->kind != 1) return 1;
     }
-    /* order: node 0, then BFS over the undirected skeleton by increasing id */
+    /* order: node 0, then BFS over the undirected skeleton by increasing id;
+     * each further component from its lowest node */
     for (i = 0; i < q->k; i++) placed[i] = -1;
-    s.order[0] = 0; placed[0] = 0; head = 0; tail = 1;
-    while (head < tail) {
-        int32_t a = s.order[head++];
-        for (j = 0; j < q->k; j++) {
-            if (j == a || placed[j] >= 0) continue;
-            if (s.qedge[a][j] == OG_NOEDGE && s.qedge[j][a] == OG_NOEDGE) continue;
-            placed[j] = tail;
-            s.order[tail++] = j;
+    tail = 0;
+    for (i = 0; i < q->k; i++) {
+        if (placed[i] >= 0) continue;
+        head = tail;
+        placed[i] = tail;
+        s.order[tail++] = i;
+        while (head < tail) {
+            int32_t a = s.order[head++];
+            for (j = 0; j < q->k; j++) {
+                if (j == a || placed[j] >= 0) continue;
+                if (s.qedge[a][j] == OG_NOEDGE && s.qedge[j][a] == OG_NOEDGE) continue;
+                placed[j] = tail;
+                s.order[tail++] = j;
+            }
         }
     }
-    if (tail != q->k) return 1;                                   /* disconnected */
     for (i = 1; i < q->k; i++) {
         int32_t u = s.order[i];
+        s.pnode[i] = -1;                                          /* starts a component */
         for (j = 0; j < i; j++) {
             int32_t w = s.order[j];
             if (s.qedge[w][u] != OG_NOEDGE) { s.pnode[i] = w; s.pout[i] = 1; break; }

@@ -167,7 +167,7 @@ def _run(og: OracleGraph, gfd, roots, induced: bool = True, count: str = "all"):
     if count == "x":
         nm = nx
     if rc != 0:
-        raise ValueError("oracle rejected the GFD (malformed or disconnected pattern)")
+        raise ValueError("oracle rejected the GFD (malformed pattern)")
     k = gfd.k
     n = int(nv.value)
     if n:
@@ -197,7 +197,7 @@ def count_within(og: OracleGraph, gfd, roots, seconds: float, induced: bool = Tr
         lib.og_free(vp)
     del keep
     if rc != 0:
-        raise ValueError("oracle rejected the GFD (malformed or disconnected pattern)")
+        raise ValueError("oracle rejected the GFD (malformed pattern)")
     return int(nm.value), int(done.value)
 
 

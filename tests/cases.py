@@ -142,3 +142,41 @@ def random_case(seed, max_k=4, n_vertices=None):
         a = int(rng.integers(0, k))
         gfd.edges.append((a, a, int(rng.choice([0, 1, -1]))))
     return g, gfd
+
+
+def random_disconnected_case(seed, max_k=4):
+    """A random tiny graph and a GFD whose pattern has at least two connected
+    components: the subgraph of G induced by k random vertices (kept only when
+    it is disconnected), labels partly generalised, random literals."""
+    rng = np.random.default_rng([779, seed])
+    while True:
+        n = int(rng.integers(5, 8))
+        g = random_small_graph(10000 + seed, n, n_vlabels=int(rng.integers(1, 3)),
+                               n_elabels=int(rng.integers(1, 3)), p_edge=float(rng.uniform(0.1, 0.35)),
+                               p_self=0.1, n_attrs=2, n_attr_values=3, p_absent=0.15)
+        src, dst, lab = g.edge_arrays()
+        E = {(int(a), int(b)): int(l) for a, b, l in zip(src, dst, lab)}
+        for _ in range(50):
+            k = int(rng.integers(2, max_k + 1))
+            vs = [int(v) for v in rng.choice(g.n_vertices, size=k, replace=False)]
+            edges = [(i, j, E[(a, b)] if rng.random() > 0.3 else -1)
+                     for i, a in enumerate(vs) for j, b in enumerate(vs) if (a, b) in E]
+            seen, stack = {0}, [0]
+            while stack:
+                x = stack.pop()
+                for (i, j, _) in edges:
+                    for (p, q) in ((i, j), (j, i)):
+                        if p == x and q not in seen:
+                            seen.add(q)
+                            stack.append(q)
+            if len(seen) < k:
+                nl = [int(g.vlabel[v]) if rng.random() > 0.3 else -1 for v in vs]
+                gfd = GFD(nl, edges, [], [], False)
+                tmp = random_pattern_gfd(rng, "tree", k, [0], [0], 2, (0, 2), 1,
+                                         lambda: int(rng.integers(0, 3)), permute=False)
+                gfd.X, gfd.Y = tmp.X, tmp.Y
+                gfd.y_false = bool(rng.random() < 0.2)
+                if gfd.y_false:
+                    gfd.Y = []
+                return g, gfd
+        seed += 1000

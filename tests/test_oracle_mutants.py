@@ -13,7 +13,10 @@ import pytest
 from oracle import oracle as O
 from oracle.bruteforce import brute_force
 
-from cases import complete_bidirected, golden_cases, out_star, random_case, star_q, undirected_q
+from synth.gfds import GFD
+
+from cases import (complete_bidirected, edges_graph, golden_cases, out_star, random_case,
+                   random_disconnected_case, star_q, undirected_q)
 
 SRC = os.path.join(os.path.dirname(O.__file__), "oracle.c")
 
@@ -41,6 +44,11 @@ MUTANTS = {
                                               "if (!og_induced) return 1;"),
     # count of X-satisfying matches
     "x_count_ignores_x": ("s->n_x_matches += (uint64_t)x_ok;", "s->n_x_matches += 1;"),
+    # disconnected patterns
+    "component_start_skips_last_vertex": ("if (s->pnode[i] < 0) { a = 0; b = g->n; hp = -1; }",
+                                          "if (s->pnode[i] < 0) { a = 0; b = g->n - 1; hp = -1; }"),
+    "component_start_uses_root_neighbours": ("        s.pnode[i] = -1;                                          /* starts a component */",
+                                             "        s.pnode[i] = 0; s.pout[i] = 1;"),
 }
 
 
@@ -73,6 +81,16 @@ def _pins_pass(lib) -> bool:
         if nm != bnm or not np.array_equal(v, bv):
             return False
     if O.validate(complete_bidirected(5), undirected_q(3, [(0, 1), (1, 2)]), lib=lib, induced=False)[0] != 60:
+        return False
+    # disconnected patterns
+    for seed in range(30):
+        g, q = random_disconnected_case(seed)
+        for induced in (True, False):
+            nm, v = O.validate(g, q, lib=lib, induced=induced)
+            bnm, bv = brute_force(g, q, induced=induced)
+            if nm != bnm or not np.array_equal(v, bv):
+                return False
+    if O.validate(edges_graph(5, []), GFD([0, 0], []), lib=lib)[0] != 20:
         return False
     # the count of X-satisfying matches
     for seed in range(80):

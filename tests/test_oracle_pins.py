@@ -208,8 +208,6 @@ def test_root_sample_partition(oracle_mod):
 def test_rejects_bad_inputs(oracle_mod):
     g = out_star(3)
     with pytest.raises(ValueError):
-        _v(oracle_mod, g, GFD([0, 0, 0], [(0, 1, 0)]))       # disconnected
-    with pytest.raises(ValueError):
         _v(oracle_mod, g, GFD([0, 0], [(0, 1, 0)], [Literal.const(0, 9, 1)]))  # bad attribute
     with pytest.raises(ValueError):
         edges_graph(2, [(0, 1, 0), (0, 1, 1)])               # repeated pair
