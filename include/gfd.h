@@ -102,7 +102,12 @@ typedef struct {
  * Directed pattern edges esrc[i] -> edst[i] with label elabel[i] (or
  * GFD_WILDCARD), at most one per ordered pair. X has nx literals, Y has ny;
  * y_false != 0 means the right-hand side is `false` (Y is then ignored).
- * Limits: 1 <= k <= GFD_MAX_K and Q connected, else GFD_ERR_UNSUPPORTED.
+ * Limits: 1 <= k <= GFD_MAX_K, else GFD_ERR_UNSUPPORTED. A disconnected Q is
+ * matched component after component (Section II's conditions hold across
+ * components too: injective, and with induced matching no G edge between the
+ * images of nodes in different components); the work grows with the product of
+ * the components' match counts, and a step whose fan-out sum exceeds 2^40
+ * returns GFD_ERR_OVERFLOW.
  */
 typedef struct {
     int32_t k;

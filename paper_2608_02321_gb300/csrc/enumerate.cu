@@ -39,6 +39,9 @@ namespace {
 
 constexpr int CTRL_THREADS = 1024;
 constexpr uint64_t LAST_LEVEL_CHUNK = 1ull << 25;  // work items per step at the last level
+// generator stored in a row for a next level that starts a pattern component:
+// its candidates are the level's candidate list (fan-out |C| for every row)
+constexpr int GEN_LIST = 4;
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
@@ -202,8 +205,11 @@ __device__ void expand_warps(const EnumArgs& A) {
         const uint64_t nrows = k == 1 ? 0 : (l == 0 ? (uint64_t)S->ncand[0]
                                                     : (uint64_t)__ldcg((const unsigned long long*)&S->nrows[l]));
         const int rw = 2 * (l + 1) + 2;  // row width at level l: ids, positions, generator, index base
+        // level 1 starts a component: root r's items are [r c1, (r+1) c1)
+        const bool list1 = k > 1 && l == 0 && LP.par < 0;
+        const uint64_t c1 = list1 ? (uint64_t)S->ncand[1] : 0;
         uint32_t rlo = 0, rhi1 = 0;
-        if (k > 1) {
+        if (k > 1 && !list1) {
             if (l == 0) {
                 rlo = warp_find(S0, 0, nrows, wb, lane);
                 rhi1 = warp_find(S0, rlo, nrows, we - 1, lane) + 1;
@@ -231,7 +237,10 @@ __device__ void expand_warps(const EnumArgs& A) {
             // lane left at the window's end checks the next prefix and falls
             // back to a binary search (root candidates may have no fan-out).
             uint64_t sr = 0;
-            if (k > 1) {
+            if (list1) {
+                r = ok ? (uint32_t)(w / c1) : 0u;
+                sr = (uint64_t)r * c1;
+            } else if (k > 1) {
                 const uint64_t widx = (uint64_t)cur + lane;
                 const uint64_t sv = widx < rhi1 ? (l == 0 ? (uint64_t)__ldg(S0 + widx) : ld_front(Sl + widx))
                                                 : ~0ull;
@@ -260,7 +269,10 @@ __device__ void expand_warps(const EnumArgs& A) {
                     uint64_t ent;  // index of the candidate's index edge
                     int choice = 0;
                     if (l == 0) {
-                        ent = w;  // the roots' index edges are level 1's, in work-item order
+                        // the roots' index edges are level 1's, in work-item order
+                        // (or level 1's candidate list when it starts a component)
+                        ent = list1 ? o : w;
+                        choice = list1 ? GEN_LIST : 0;
                         m[0] = (uint32_t)D->cand[0][r];
                     } else {
                         rowp = rows_l + (uint64_t)r * rw;
@@ -274,6 +286,10 @@ __device__ void expand_warps(const EnumArgs& A) {
                         const int2 e = __ldg(D->cpi_idx[i] + ent);
                         j = e.x;
                         v = (uint32_t)e.y;
+                    } else if (choice == GEN_LIST) {
+                        // the level starts a component: its candidate list
+                        j = (int32_t)ent;
+                        v = (uint32_t)__ldg(D->cand[i] + ent);
                     } else {
                         // candidates from the adjacency of the other end of a
                         // required back edge (the shorter list): keep those in
@@ -378,10 +394,16 @@ __device__ void expand_warps(const EnumArgs& A) {
                 if (ok) {
                     const LevelPlan& L2 = D->lv[i + 1];
                     const int pn = L2.par;
-                    const uint32_t ppn = pn == i ? (uint32_t)j : (l == 0 ? r : (uint32_t)rowp[l + 1 + pn]);
-                    const uint32_t* co = D->cpi_off[i + 1];
-                    nbase = __ldg(co + ppn);
-                    fo = __ldg(co + ppn + 1) - nbase;
+                    if (pn < 0) {
+                        // level i+1 starts a component: its whole candidate list
+                        gen = GEN_LIST;
+                        fo = S->ncand[i + 1];
+                    } else {
+                        const uint32_t ppn = pn == i ? (uint32_t)j : (l == 0 ? r : (uint32_t)rowp[l + 1 + pn]);
+                        const uint32_t* co = D->cpi_off[i + 1];
+                        nbase = __ldg(co + ppn);
+                        fo = __ldg(co + ppn + 1) - nbase;
+                    }
                     for (int q = 0; q < L2.ngen; q++) {
                         const int cg = L2.gen[q];
                         const uint32_t x = m[L2.chk_q[cg]];
@@ -446,7 +468,9 @@ __device__ void slot_start(const SlotDesc* D, SlotState* S) {
     S->cursor[0] = 0;
     S->cb = S->ce = 0;
     S->nrows[0] = S->ncand[0];
-    S->total[0] = D->k == 1 ? (uint64_t)S->ncand[0] : (uint64_t)D->cpi_off[1][S->ncand[0]];
+    S->total[0] = D->k == 1             ? (uint64_t)S->ncand[0]
+                : D->lv[1].par < 0      ? (uint64_t)S->ncand[0] * S->ncand[1]  // level 1 starts a component
+                                        : (uint64_t)D->cpi_off[1][S->ncand[0]];
 }
 
 // One block: finish the last step of every slot and plan the next one.

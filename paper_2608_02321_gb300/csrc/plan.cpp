@@ -93,24 +93,27 @@ int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostP
             deg[a] += adj[a][b];
         }
     }
-    {  // connected?
-        bool seen[MAXK] = {false};
-        int stack[MAXK], sp = 0, cnt = 1;
-        seen[0] = true;
-        stack[sp++] = 0;
+    // connected components of the skeleton (a disconnected pattern is matched
+    // component after component; its levels that start a component have no
+    // tree parent and take their candidates from the candidate list)
+    int comp[MAXK], ncomp = 0, comp_size[MAXK];
+    for (int a = 0; a < k; a++) comp[a] = -1;
+    for (int a0 = 0; a0 < k; a0++) {
+        if (comp[a0] >= 0) continue;
+        int stack[MAXK], sp = 0;
+        comp[a0] = ncomp;
+        comp_size[ncomp] = 1;
+        stack[sp++] = a0;
         while (sp) {
-            int a = stack[--sp];
+            const int a = stack[--sp];
             for (int b = 0; b < k; b++)
-                if (adj[a][b] && !seen[b]) {
-                    seen[b] = true;
-                    cnt++;
+                if (adj[a][b] && comp[b] < 0) {
+                    comp[b] = ncomp;
+                    comp_size[ncomp]++;
                     stack[sp++] = b;
                 }
         }
-        if (cnt != k) {
-            set_error(GFD_ERR_UNSUPPORTED, "pattern is disconnected");
-            return GFD_ERR_UNSUPPORTED;
-        }
+        ncomp++;
     }
     // 2-core by repeated removal of vertices of degree <= 1
     bool core[MAXK];
@@ -132,8 +135,8 @@ int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostP
                 }
         }
     }
-    bool any_core = false;
-    for (int a = 0; a < k; a++) any_core |= core[a];
+    bool any_core[MAXK] = {false};  // per component
+    for (int a = 0; a < k; a++) any_core[comp[a]] |= core[a];
     // ---- cost model: log of the expected number of maps of the subpattern on
     // a node set (degrees counted inside the set only)
     const double NEG = -std::numeric_limits<double>::infinity();
@@ -199,28 +202,52 @@ int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostP
             if (phase == 0) *core_end = nord;
             if (phase == 1) *forest_end = nord;
         }
-        return nord == k ? cost : std::numeric_limits<double>::infinity();
+        return nord == comp_size[comp[root]] ? cost : std::numeric_limits<double>::infinity();
     };
-    int best_root = -1;
-    double best_cost = 0;
-    for (int r = 0; r < k; r++) {
-        if (any_core && !core[r]) continue;
-        int ord[MAXK], ce = 0, fe = 0;
-        const double c = greedy(r, ord, &ce, &fe);
-        if (best_root < 0 || c < best_cost) {
-            best_root = r;
-            best_cost = c;
+    // per component the root of least cost and its greedy order
+    int best_root[MAXK];
+    double best_cost[MAXK];
+    for (int c = 0; c < ncomp; c++) {
+        best_root[c] = -1;
+        best_cost[c] = 0;
+        for (int r = 0; r < k; r++) {
+            if (comp[r] != c || (any_core[c] && !core[r])) continue;
+            int ord[MAXK], ce = 0, fe = 0;
+            const double cost = greedy(r, ord, &ce, &fe);
+            if (best_root[c] < 0 || cost < best_cost[c]) {
+                best_root[c] = r;
+                best_cost[c] = cost;
+            }
         }
     }
+    // components with fewer expected matches first (their matches are the
+    // rows the later components multiply)
+    double comp_est[MAXK];
+    for (int c = 0; c < ncomp; c++) {
+        bool in[MAXK] = {false};
+        for (int a = 0; a < k; a++) in[a] = comp[a] == c;
+        comp_est[c] = log_est(in);
+    }
+    int corder[MAXK];
+    for (int c = 0; c < ncomp; c++) corder[c] = c;
+    std::stable_sort(corder, corder + ncomp, [&](int a, int b) { return comp_est[a] < comp_est[b]; });
     {
-        int ce = 0, fe = 0;
-        if (greedy(best_root, P->order, &ce, &fe) == std::numeric_limits<double>::infinity()) {
-            set_error(GFD_ERR_INVALID_ARG, "internal: order incomplete");
-            return GFD_ERR_INVALID_ARG;
+        int at = 0;
+        for (int t = 0; t < ncomp; t++) {
+            const int c = corder[t];
+            int ce = 0, fe = 0;
+            if (greedy(best_root[c], P->order + at, &ce, &fe) == std::numeric_limits<double>::infinity()) {
+                set_error(GFD_ERR_INVALID_ARG, "internal: order incomplete");
+                return GFD_ERR_INVALID_ARG;
+            }
+            if (t == 0) {
+                P->core_size = ce;
+                P->forest_end = fe;
+            }
+            at += comp_size[c];
         }
-        P->core_size = ce;
-        P->forest_end = fe;
     }
+    P->n_components = ncomp;
     P->k = k;
     for (int i = 0; i < k; i++) P->level_of[P->order[i]] = i;
 
@@ -236,14 +263,16 @@ int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostP
                     L.par = (int8_t)h;
                     break;
                 }
-            const int p = P->order[L.par];
-            if (q[p][u] != NOEDGE) {
-                L.tdir = 1;
-                L.tlab = q[p][u];
-            } else {
-                L.tdir = 0;
-                L.tlab = q[u][p];
-            }
+            if (L.par >= 0) {
+                const int p = P->order[L.par];
+                if (q[p][u] != NOEDGE) {
+                    L.tdir = 1;
+                    L.tlab = q[p][u];
+                } else {
+                    L.tdir = 0;
+                    L.tlab = q[u][p];
+                }
+            }  // else: u starts a component
         }
         // pair checks against every earlier level
         int n = 0;

@@ -25,6 +25,8 @@ struct HostPlan {
     int level_of[MAXK];   // level of node
     int core_size = 0;    // levels [0, core_size) are the core (2-core, or the root)
     int forest_end = 0;   // levels [core_size, forest_end) are forest nodes, the rest leaves
+                          // (of the first component)
+    int n_components = 1; // skeleton components, matched one after another
     LevelPlan lv[MAXK];
     FilterKey key[MAXK];  // candidate filter key per level
     std::vector<Con> td[MAXK];  // constraints from earlier levels

@@ -326,6 +326,7 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
         }
         for (int i = 1; i < P.k; i++) {
             const int par = P.lv[i].par;
+            if (par < 0) continue;  // starts a component: no index edges
             const int32_t plab = phis[s]->node_label[P.order[par]];
             D.cpi_cap[i] = std::min<uint64_t>(lab_deg(plab, P.lv[i].tdir == 1), (uint64_t)g->m);
             F.cpi_off[i] = L.take(4ull * (D.cand_cap[par] + 1ull));
@@ -344,7 +345,7 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
     size_t n_compact = 0, n_cpi = 0, n_and = 0, n_sct = 0, n_prn = 0;
     for (int s = 0; s < n; s++) {
         const HostPlan& P = G->plans[s];
-        n_cpi += P.k - 1;
+        for (int i = 1; i < P.k; i++) n_cpi += P.lv[i].par >= 0;
         n_and += P.k;
         n_compact += P.k;
         for (int i = 0; i < P.k; i++) {
@@ -360,7 +361,8 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
     uint64_t max_pcand = 0;
     for (int s = 0; s < n; s++)
         for (int i = 1; i < G->plans[s].k; i++)
-            max_pcand = std::max<uint64_t>(max_pcand, G->descs[s].cand_cap[G->plans[s].lv[i].par]);
+            if (G->plans[s].lv[i].par >= 0)
+                max_pcand = std::max<uint64_t>(max_pcand, G->descs[s].cand_cap[G->plans[s].lv[i].par]);
     G->cpi_nch = cpi_chunks(max_pcand);
     G->o_cmp_sums = L.take(4ull * G->cmp_chunks * std::max<size_t>(1, n_compact));
     G->o_cpi_sums = L.take(8ull * G->cpi_nch * std::max<size_t>(1, n_cpi));
@@ -397,7 +399,7 @@ int group_build(gfd_graph* g, Group* G, const Tables& T, bool refine, cudaStream
             D.rank[i] = (uint32_t*)(base + F.rank[i]);
             D.cand[i] = (int32_t*)(base + F.cand[i]);
             if (i >= 1) {
-                D.cpi_off[i] = (uint32_t*)(base + F.cpi_off[i]);
+                D.cpi_off[i] = P.lv[i].par >= 0 ? (uint32_t*)(base + F.cpi_off[i]) : nullptr;
                 D.cpi_idx[i] = nullptr;  // allocated once the index edges are counted
             }
         }
@@ -551,6 +553,7 @@ int group_build(gfd_graph* g, Group* G, const Tables& T, bool refine, cudaStream
     for (int s = 0; s < n; s++)
         for (int i = 1; i < G->plans[s].k; i++) {
             const int par = G->plans[s].lv[i].par;
+            if (par < 0) continue;  // starts a component
             CpiJob J{};
             J.pcand = G->descs[s].cand[par];
             J.pcount = state_ncand(s, par);
@@ -653,11 +656,13 @@ int group_launch(gfd_graph* g, Group* G, const Tables& T, cudaMemPool_t pool, cu
         G->cpi_bytes = bytes;
         int j = 0;
         for (int s = 0; s < G->n; s++)
-            for (int i = 1; i < G->plans[s].k; i++, j++) {
+            for (int i = 1; i < G->plans[s].k; i++) {
+                if (G->plans[s].lv[i].par < 0) continue;  // same jobs, same order as built
                 int2* idx = (int2*)(G->cpi_base + at[j]);
                 G->cpi_jobs[j].idx = idx;
                 G->cpi_jobs[j].cap = tot[j];
                 G->descs[s].cpi_idx[i] = idx;
+                j++;
             }
         GFD_CUDA(cudaMemcpyAsync(d_cpi, G->cpi_jobs.data(), sizeof(CpiJob) * ncpi, cudaMemcpyHostToDevice, st));
         for (int s = 0; s < G->n; s++)

@@ -182,8 +182,8 @@ def test_rejects_invalid_inputs(lib):
     g = out_star(4)
     dg = gpu_graph(g)
     with pytest.raises(G.GfdError) as e:
-        dg.validate(GFD([0, 0, 0], [(0, 1, 0)]))
-    assert e.value.code == G.GFD_ERR_UNSUPPORTED                      # disconnected
+        dg.validate(GFD([0] * 17, [(i, i + 1, 0) for i in range(16)]))
+    assert e.value.code == G.GFD_ERR_UNSUPPORTED                      # k > 16
     with pytest.raises(G.GfdError) as e:
         dg.validate(GFD([0, 0], [(0, 1, 0)], [Literal.const(0, 5, 1)]))
     assert e.value.code == G.GFD_ERR_INVALID_ARG                      # no attribute 5
