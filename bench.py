@@ -236,7 +236,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-non-induced", action="store_true",
-                    help="skip the non-induced and X-pushdown legs")
+                    help="skip the non-induced, X-pushdown and disconnected-pattern legs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flags", type=int, default=0)
     ap.add_argument("--budget-gb", type=float, default=0.0,
@@ -429,6 +429,49 @@ def main():
             line["same_violation_count_as_headline"] = line["violations_per_step"] == viols
             push_x = line
 
+    # disconnected patterns: unions of two batched GFDs with few matches each
+    # (the product of the two match counts bounds the union's), one batch
+    disconnected = None
+    if not args.no_non_induced and len(qs) > 1:
+        from synth.gfds import GFD as _GFD
+        counts = [r.n_matches for r in stats]
+        order = [i for i in sorted(range(len(qs)), key=lambda i: counts[i]) if 1000 <= counts[i] <= 200000]
+        unions, used = [], set()
+        for a in order:
+            if len(unions) == 16:
+                break
+            if a in used:
+                continue
+            for b in order:
+                if b != a and b not in used and counts[a] * counts[b] <= 3e7:
+                    qa, qb = qs[a], qs[b]
+                    ka = qa.k
+                    unions.append(_GFD(list(qa.node_label) + list(qb.node_label),
+                                       list(qa.edges) + [(x + ka, y + ka, l) for (x, y, l) in qb.edges],
+                                       qa.X, qa.Y, qa.y_false, name=f"{qa.name}+{qb.name}"))
+                    used.update((a, b))
+                    break
+        if unions:
+            res = dg.validate_batch(unions, stream=stream, flags=flags, max_violations_hint=hint)
+            dtimes = []
+            for _ in range(max(1, min(2, args.steps))):
+                l2_flush.zero_()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                res = dg.validate_batch(unions, stream=stream, flags=flags, max_violations_hint=hint)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                dtimes.append(e0.elapsed_time(e1))
+            dm = sum(r.n_matches for r in res)
+            dms = float(np.mean(dtimes))
+            disconnected = {"value": dm / (dms / 1000.0), "unit": UNIT, "ms_per_step": dms,
+                            "gfds": len(unions), "matches_per_step": dm,
+                            "violations_per_step": sum(r.n_violations for r in res),
+                            "recipe": "pairs of batched GFDs with 1e3-2e5 matches each and a product <= 3e7, "
+                                      "joined as two components (X and Y of the first)"}
+
     # serving: a Poisson stream of single-GFD requests against the resident
     # graph, continuous batching vs one gfd_validate per request
     serving = None
@@ -466,7 +509,7 @@ def main():
                                                   "every timed step",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "plain": plain, "non_induced": non_induced, "push_x": push_x, "serving": serving, "autotuned": tuned,
+                "clocks": clk, "plain": plain, "non_induced": non_induced, "push_x": push_x, "disconnected": disconnected, "serving": serving, "autotuned": tuned,
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,
                 "matches_per_step": matches, "violations_per_step": viols,
                 "work_items_per_step": work, "edge_probes_per_step": probes,

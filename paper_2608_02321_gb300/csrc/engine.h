@@ -141,8 +141,10 @@ int launch_split(const SlotDesc* slots, const int32_t* arena, uint64_t n, int32_
 // launch; else a host loop (optionally captured into CUDA graphs). variant:
 // 0 (256 threads, >= 4 blocks/SM), 1 (256, >= 6), 2 (256, >= 8), 3 (128, >= 12),
 // 4 (128, >= 16), 5 (512, >= 3).
-int enum_run(const EnumArgs& a, bool persistent, bool use_graph, int variant, cudaStream_t st, cudaEvent_t ev0,
-             cudaEvent_t ev1, int64_t* launches);
+// general: some slot has a pattern component that starts after level 0 or X
+// pushed down (the expansion compiled with those paths); else the leaner one.
+int enum_run(const EnumArgs& a, bool persistent, bool use_graph, int variant, bool general, cudaStream_t st,
+             cudaEvent_t ev0, cudaEvent_t ev1, int64_t* launches);
 int variant_threads(int variant);
 constexpr int N_VARIANTS = 6;
 

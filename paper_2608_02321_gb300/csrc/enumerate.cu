@@ -179,6 +179,10 @@ __device__ __forceinline__ uint64_t warp_excl_scan(uint64_t x, int lane, uint64_
 // work items (no block-wide barrier in the loop). A tile belongs to one slot
 // and one level; the warp finds them (and the rows the tile covers) with
 // lane-parallel searches, then processes 32 work items per iteration.
+// GEN = false: the common case (connected patterns, X checked at the last
+// level only), compiled without the general paths so that it keeps its
+// registers; GEN = true adds component starts and X pushed down.
+template <bool GEN>
 __device__ void expand_warps(const EnumArgs& A) {
     const int lane = threadIdx.x & 31;
     const uint64_t gwarp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
@@ -206,7 +210,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                                                     : (uint64_t)__ldcg((const unsigned long long*)&S->nrows[l]));
         const int rw = 2 * (l + 1) + 2;  // row width at level l: ids, positions, generator, index base
         // level 1 starts a component: root r's items are [r c1, (r+1) c1)
-        const bool list1 = k > 1 && l == 0 && LP.par < 0;
+        const bool list1 = GEN && k > 1 && l == 0 && LP.par < 0;
         const uint64_t c1 = list1 ? (uint64_t)S->ncand[1] : 0;
         uint32_t rlo = 0, rhi1 = 0;
         if (k > 1 && !list1) {
@@ -286,7 +290,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                         const int2 e = __ldg(D->cpi_idx[i] + ent);
                         j = e.x;
                         v = (uint32_t)e.y;
-                    } else if (choice == GEN_LIST) {
+                    } else if (GEN && choice == GEN_LIST) {
                         // the level starts a component: its candidate list
                         j = (int32_t)ent;
                         v = (uint32_t)__ldg(D->cand[i] + ent);
@@ -340,7 +344,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                 m[i] = v;
                 // X pushed down: the X literals whose ends are matched at this
                 // level (before the last one; the last level checks its own below)
-                if (ok && D->push_x && !last)
+                if (GEN && ok && D->push_x && !last)
                     for (int q = 0; q < D->nx && ok; q++)
                         if (D->lit[q].lvl == i) ok = lit_holds(g, D->lit[q], m);
             }
@@ -351,8 +355,9 @@ __device__ void expand_warps(const EnumArgs& A) {
                 if (ok) {
                     bool x_ok = true;
                     for (int q = 0; q < D->nx && x_ok; q++)
-                        if (D->lit[q].lvl == i) x_ok = lit_holds(g, D->lit[q], m);
-                    tile_matches += x_ok || !D->push_x;
+                        if (!GEN || D->lit[q].lvl == i) x_ok = lit_holds(g, D->lit[q], m);
+                    if (GEN) tile_matches += x_ok || !D->push_x;
+                    else tile_matches++;
                     if (x_ok) {
                         bool y_ok = !D->y_false;
                         for (int q = 0; q < D->ny && y_ok; q++) y_ok = lit_holds(g, D->lit[D->nx + q], m);
@@ -394,7 +399,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                 if (ok) {
                     const LevelPlan& L2 = D->lv[i + 1];
                     const int pn = L2.par;
-                    if (pn < 0) {
+                    if (GEN && pn < 0) {
                         // level i+1 starts a component: its whole candidate list
                         gen = GEN_LIST;
                         fo = S->ncand[i + 1];
@@ -573,9 +578,9 @@ __global__ void __launch_bounds__(CTRL_THREADS) k_control(EnumArgs A, int first)
     control_step<CTRL_THREADS>(A, first != 0);
 }
 
-template <int NT, int MINB>
+template <int NT, int MINB, bool GEN>
 __global__ void __launch_bounds__(NT, MINB) k_expand(EnumArgs A) {
-    expand_warps(A);
+    expand_warps<GEN>(A);
 }
 
 // Bounded grid barrier (cooperative launch guarantees co-residency): the last
@@ -616,10 +621,10 @@ __device__ bool grid_barrier(Sched* s) {
     return ok_s != 0;
 }
 
-template <int NT, int MINB>
+template <int NT, int MINB, bool GEN>
 __global__ void __launch_bounds__(NT, MINB) k_persistent(EnumArgs A) {
     for (;;) {
-        expand_warps(A);
+        expand_warps<GEN>(A);
         if (!grid_barrier(A.sched)) return;
         if (blockIdx.x == 0) control_step<NT>(A, false);
         if (!grid_barrier(A.sched)) return;
@@ -627,12 +632,12 @@ __global__ void __launch_bounds__(NT, MINB) k_persistent(EnumArgs A) {
     }
 }
 
-template <int NT, int MINB>
+template <int NT, int MINB, bool GEN>
 int launch_persistent(const EnumArgs& a, cudaStream_t st, int64_t* launches) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<NT, MINB>, NT, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<NT, MINB, GEN>, NT, 0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm < 1) {
         set_error(GFD_ERR_CUDA, "persistent enumeration kernel cannot be resident");
@@ -642,24 +647,24 @@ int launch_persistent(const EnumArgs& a, cudaStream_t st, int64_t* launches) {
     EnumArgs args = a;
     args.n_warps = grid * (NT / 32);
     void* params[] = {&args};
-    e = cudaLaunchCooperativeKernel((const void*)k_persistent<NT, MINB>, dim3(grid), dim3(NT), params, 0, st);
+    e = cudaLaunchCooperativeKernel((const void*)k_persistent<NT, MINB, GEN>, dim3(grid), dim3(NT), params, 0, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel");
     if (launches) *launches += 1;
     return GFD_OK;
 }
 
-template <int NT, int MINB>
+template <int NT, int MINB, bool GEN>
 int expand_grid() {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand<NT, MINB>, NT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand<NT, MINB, GEN>, NT, 0);
     return sms * std::max(per_sm, 1);
 }
 
-template <int NT, int MINB>
+template <int NT, int MINB, bool GEN>
 int host_loop(const EnumArgs& a0, bool use_graph, cudaStream_t st, int64_t* launches) {
-    const int grid = expand_grid<NT, MINB>();
+    const int grid = expand_grid<NT, MINB, GEN>();
     EnumArgs a = a0;
     a.n_warps = grid * (NT / 32);
     int32_t* h_active = nullptr;
@@ -673,7 +678,7 @@ int host_loop(const EnumArgs& a0, bool use_graph, cudaStream_t st, int64_t* laun
         e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             for (int it = 0; it < per_check; it++) {
-                k_expand<NT, MINB><<<grid, NT, 0, st>>>(a);
+                k_expand<NT, MINB, GEN><<<grid, NT, 0, st>>>(a);
                 k_control<<<1, CTRL_THREADS, 0, st>>>(a, 0);
             }
             e = cudaStreamEndCapture(st, &graph);
@@ -691,7 +696,7 @@ int host_loop(const EnumArgs& a0, bool use_graph, cudaStream_t st, int64_t* laun
             if (launches) *launches += 2 * per_check;
         } else {
             for (int it = 0; it < per_check; it++) {
-                k_expand<NT, MINB><<<grid, NT, 0, st>>>(a);
+                k_expand<NT, MINB, GEN><<<grid, NT, 0, st>>>(a);
                 k_control<<<1, CTRL_THREADS, 0, st>>>(a, 0);
             }
             e = cudaGetLastError();
@@ -782,15 +787,15 @@ int launch_split(const SlotDesc* slots, const int32_t* arena, uint64_t n, int32_
 
 namespace {
 
-template <int NT, int MINB>
+template <int NT, int MINB, bool GEN>
 int capture_steps_t(const EnumArgs& a0, int steps, cudaStream_t st, cudaGraph_t* graph, cudaGraphExec_t* exec) {
-    const int grid = expand_grid<NT, MINB>();
+    const int grid = expand_grid<NT, MINB, GEN>();
     EnumArgs a = a0;
     a.n_warps = grid * (NT / 32);
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         for (int it = 0; it < steps; it++) {
-            k_expand<NT, MINB><<<grid, NT, 0, st>>>(a);
+            k_expand<NT, MINB, GEN><<<grid, NT, 0, st>>>(a);
             k_control<<<1, CTRL_THREADS, 0, st>>>(a, 0);
         }
         e = cudaStreamEndCapture(st, graph);
@@ -800,9 +805,9 @@ int capture_steps_t(const EnumArgs& a0, int steps, cudaStream_t st, cudaGraph_t*
     return GFD_OK;
 }
 
-template <int NT, int MINB>
+template <int NT, int MINB, bool GEN>
 int run_variant(const EnumArgs& a, bool persistent, bool use_graph, cudaStream_t st, int64_t* launches) {
-    return persistent ? launch_persistent<NT, MINB>(a, st, launches) : host_loop<NT, MINB>(a, use_graph, st, launches);
+    return persistent ? launch_persistent<NT, MINB, GEN>(a, st, launches) : host_loop<NT, MINB, GEN>(a, use_graph, st, launches);
 }
 
 }  // namespace
@@ -819,15 +824,34 @@ int variant_threads(int v) {
 
 int capture_steps(const EnumArgs& a, int variant, int steps, cudaStream_t st, cudaGraph_t* graph,
                   cudaGraphExec_t* exec) {
+    // a session admits any request later: the general expansion
+    constexpr bool GEN = true;
     switch (variant) {
-        case 1: return capture_steps_t<256, 6>(a, steps, st, graph, exec);
-        case 2: return capture_steps_t<256, 8>(a, steps, st, graph, exec);
-        case 3: return capture_steps_t<128, 12>(a, steps, st, graph, exec);
-        case 4: return capture_steps_t<128, 16>(a, steps, st, graph, exec);
-        case 5: return capture_steps_t<512, 3>(a, steps, st, graph, exec);
-        default: return capture_steps_t<256, 4>(a, steps, st, graph, exec);
+        case 1: return capture_steps_t<256, 6, GEN>(a, steps, st, graph, exec);
+        case 2: return capture_steps_t<256, 8, GEN>(a, steps, st, graph, exec);
+        case 3: return capture_steps_t<128, 12, GEN>(a, steps, st, graph, exec);
+        case 4: return capture_steps_t<128, 16, GEN>(a, steps, st, graph, exec);
+        case 5: return capture_steps_t<512, 3, GEN>(a, steps, st, graph, exec);
+        default: return capture_steps_t<256, 4, GEN>(a, steps, st, graph, exec);
     }
 }
+
+namespace {
+
+template <bool GEN>
+int run_any_variant(const EnumArgs& a, bool persistent, bool use_graph, int variant, cudaStream_t st,
+                    int64_t* launches) {
+    switch (variant) {
+        case 1: return run_variant<256, 6, GEN>(a, persistent, use_graph, st, launches);
+        case 2: return run_variant<256, 8, GEN>(a, persistent, use_graph, st, launches);
+        case 3: return run_variant<128, 12, GEN>(a, persistent, use_graph, st, launches);
+        case 4: return run_variant<128, 16, GEN>(a, persistent, use_graph, st, launches);
+        case 5: return run_variant<512, 3, GEN>(a, persistent, use_graph, st, launches);
+        default: return run_variant<256, 4, GEN>(a, persistent, use_graph, st, launches);
+    }
+}
+
+}  // namespace
 
 int enum_init(const EnumArgs& a, cudaStream_t st) {
     k_control<<<1, CTRL_THREADS, 0, st>>>(a, 1);
@@ -835,18 +859,11 @@ int enum_init(const EnumArgs& a, cudaStream_t st) {
     return e == cudaSuccess ? GFD_OK : cuda_fail(e, "k_control");
 }
 
-int enum_run(const EnumArgs& a, bool persistent, bool use_graph, int variant, cudaStream_t st, cudaEvent_t ev0,
-             cudaEvent_t ev1, int64_t* launches) {
+int enum_run(const EnumArgs& a, bool persistent, bool use_graph, int variant, bool general, cudaStream_t st,
+             cudaEvent_t ev0, cudaEvent_t ev1, int64_t* launches) {
     if (ev0) cudaEventRecord(ev0, st);
-    int rc;
-    switch (variant) {
-        case 1: rc = run_variant<256, 6>(a, persistent, use_graph, st, launches); break;
-        case 2: rc = run_variant<256, 8>(a, persistent, use_graph, st, launches); break;
-        case 3: rc = run_variant<128, 12>(a, persistent, use_graph, st, launches); break;
-        case 4: rc = run_variant<128, 16>(a, persistent, use_graph, st, launches); break;
-        case 5: rc = run_variant<512, 3>(a, persistent, use_graph, st, launches); break;
-        default: rc = run_variant<256, 4>(a, persistent, use_graph, st, launches); break;
-    }
+    const int rc = general ? run_any_variant<true>(a, persistent, use_graph, variant, st, launches)
+                           : run_any_variant<false>(a, persistent, use_graph, variant, st, launches);
     if (ev1) cudaEventRecord(ev1, st);
     return rc;
 }

@@ -55,7 +55,7 @@ __global__ void k_filter(DevGraph g, const FilterKey* __restrict__ keys, int nke
         dout -= has_self;
         din -= has_self;
         for (int k = 0; k < nkeys; k++) {
-            const FilterKey key = sk[k];
+            const FilterKey& key = sk[k];  // fields read from shared memory as needed
             bool self_ok = key.self_exp == EXP_SKIP ? true
                          : key.self_exp == EXP_NONE ? !has_self
                          : key.self_exp == EXP_ANY  ? has_self

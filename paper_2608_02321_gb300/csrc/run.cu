@@ -767,8 +767,11 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
     if (lrc) return lrc;
     const EnumArgs A = enum_args(g, T);
     if (int rc = enum_init(A, st)) return rc;
-    if (int rc = enum_run(A, persistent, use_graph, variant, st, prof.on ? prof.ev[2 * PROF_ENUM] : nullptr,
-                          prof.on ? prof.ev[2 * PROF_ENUM + 1] : nullptr, &launches[PROF_ENUM]))
+    bool general = false;  // any slot needing the general expansion
+    for (int s = 0; s < n; s++) general |= G.plans[s].push_x || G.plans[s].n_components > 1;
+    if (int rc = enum_run(A, persistent, use_graph, variant, general, st,
+                          prof.on ? prof.ev[2 * PROF_ENUM] : nullptr, prof.on ? prof.ev[2 * PROF_ENUM + 1] : nullptr,
+                          &launches[PROF_ENUM]))
         return rc;
     launches[PROF_ENUM] += 1;
 
