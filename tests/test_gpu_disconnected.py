@@ -90,3 +90,25 @@ def test_batch_mixing_connected_and_disconnected(lib, oracle_mod):
     res = dg.validate_batch(qs)
     for i, q in enumerate(qs):
         assert_same((res[i].n_matches, res[i].violations()), oracle_mod.validate(g, q), f"gfd {i}")
+
+
+def test_session_mixing_connected_and_disconnected(lib, oracle_mod):
+    """A serving session (always the general expansion) with connected and
+    disconnected requests interleaved, in both matching modes."""
+    g = random_small_graph(4343, 9, n_vlabels=2, n_elabels=2, p_edge=0.3, p_self=0.1,
+                           n_attrs=2, n_attr_values=3, p_absent=0.15)
+    reqs = []
+    for s in range(10):
+        reqs.append(random_disconnected_case(s)[1])
+        reqs.append(random_case(s)[1])
+    dg = gpu_graph(g)
+    for flags, induced in ((0, True), (G.FLAG_NON_INDUCED, False)):
+        sess = G.Session(dg, max_slots=3, frontier_budget_bytes=64 << 20, max_violations_hint=1 << 12, flags=flags)
+        ids = {sess.submit(q): i for i, q in enumerate(reqs)}
+        got = {}
+        while len(got) < len(reqs):
+            sess.step()
+            for rid, res in sess.results():
+                got[ids[rid]] = (res.n_matches, res.violations())
+        for i, q in enumerate(reqs):
+            assert_same(got[i], oracle_mod.validate(g, q, induced=induced), f"request {i} flags {flags}")
