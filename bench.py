@@ -500,6 +500,10 @@ def main():
         cpu = {"value": m / t if t > 0 else 0.0, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{r} random root vertices (images of pattern node 0) over all {len(qs)} GFDs, "
                          f"{t:.1f} s wall"}
+        # the same at one thread (a shorter sample)
+        m1, t1, r1 = oracle_sample(g, qs, max(2.0, args.cpu_seconds / 4), 1, seed=11)
+        cpu["one_thread"] = {"value": m1 / t1 if t1 > 0 else 0.0, "unit": UNIT, "cores": 1,
+                             "sample": f"{r1} random root vertices, {t1:.1f} s wall"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
