@@ -102,17 +102,29 @@ struct CpiJob {          // index edges of one spanning-tree edge
     uint64_t* csum;          // per-chunk count sums (scratch)
 };
 
+// Adjacency lists longer than HUB_LIST entries (hubs of a skewed degree
+// distribution) are queued by the warp kernels and scanned afterwards by whole
+// blocks, so that one hub does not leave a single warp running long after the
+// rest of the launch; a full queue leaves the list to its warp.
+constexpr uint32_t HUB_LIST = 4096;
+constexpr uint32_t HUB_CAP = 1u << 19;
+struct HubQueue {
+    unsigned long long* item;  // (job << 40) | (constraint << 32) | candidate index
+    uint32_t* n;               // items queued (may exceed cap: only cap are stored)
+    uint32_t cap;
+};
+
 // ---- index kernels (index.cu); each launch covers all jobs given
 int launch_filter(const DevGraph& g, const FilterKey* d_keys, int nkeys, uint32_t* d_out, cudaStream_t st);
 int launch_and(const DevGraph& g, const AndJob* d_jobs, int njobs, cudaStream_t st);
 int launch_compact(const DevGraph& g, const CompactJob* d_jobs, int njobs, cudaStream_t st);
-int launch_scatter(const DevGraph& g, const ScatterJob* d_jobs, int njobs, cudaStream_t st);
-int launch_prune(const DevGraph& g, const PruneJob* d_jobs, int njobs, cudaStream_t st);
+int launch_scatter(const DevGraph& g, const ScatterJob* d_jobs, int njobs, const HubQueue& hq, cudaStream_t st);
+int launch_prune(const DevGraph& g, const PruneJob* d_jobs, int njobs, const HubQueue& hq, cudaStream_t st);
 // Index edges in two launches: counts, offsets and per-job totals first (the
 // caller reads the totals back and allocates exactly), then the fill.
 int launch_cpi_count(const DevGraph& g, const CpiJob* d_jobs, int njobs, uint32_t nchunks, int32_t* d_err,
-                     uint32_t* d_totals, cudaStream_t st);
-int launch_cpi_fill(const DevGraph& g, const CpiJob* d_jobs, int njobs, cudaStream_t st);
+                     uint32_t* d_totals, const HubQueue& hq, cudaStream_t st);
+int launch_cpi_fill(const DevGraph& g, const CpiJob* d_jobs, int njobs, const HubQueue& hq, cudaStream_t st);
 uint32_t compact_chunks(const DevGraph& g);
 uint32_t cpi_chunks(uint64_t max_parent_candidates);
 

@@ -159,12 +159,34 @@ constexpr uint32_t SHORT_LIST = 32;
 // rather than two per entry.
 constexpr int UNROLL = 4;
 
+constexpr int HUB_THREADS = 512;
+constexpr int HUB_GRID = 152 * 4;  // blocks of the hub kernels (grid-stride over the queue)
+
+// Queue the lanes whose list is a hub (warp-synchronous: every lane calls it);
+// true for the lanes whose item was stored.
+__device__ __forceinline__ bool hub_push(const HubQueue& q, bool want, unsigned long long item, int lane) {
+    const uint32_t b = __ballot_sync(0xffffffffu, want);
+    if (!b) return false;
+    const int leader = __ffs(b) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(q.n, (uint32_t)__popc(b));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    const uint32_t pos = base + __popc(b & ((1u << lane) - 1u));
+    if (want && pos < q.cap) {
+        q.item[pos] = item;
+        return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint32_t hub_count(const HubQueue& q) { return min(*q.n, q.cap); }
+
 __device__ __forceinline__ void load_group(const uint32_t* adj, uint32_t e, uint32_t e1, uint32_t (&p)[UNROLL]) {
 #pragma unroll
     for (int t = 0; t < UNROLL; t++) p[t] = e + t < e1 ? __ldg(adj + e + t) : 0u;
 }
 
-__global__ void k_scatter(DevGraph g, const ScatterJob* __restrict__ jobs, int njobs) {
+__global__ void k_scatter(DevGraph g, const ScatterJob* __restrict__ jobs, int njobs, HubQueue hq) {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
     for (int j = 0; j < njobs; j++) {
@@ -181,6 +203,7 @@ __global__ void k_scatter(DevGraph g, const ScatterJob* __restrict__ jobs, int n
                 e0 = off[v];
                 e1 = off[v + 1];
             }
+            if (hub_push(hq, e1 - e0 > HUB_LIST, ((unsigned long long)j << 40) | a, lane)) e1 = e0;
             const bool is_long = e1 - e0 > SHORT_LIST;
             if (!is_long)
                 for (uint32_t e = e0; e < e1; e += UNROLL) {
@@ -242,7 +265,7 @@ __device__ __forceinline__ bool any_hit_warp(const DevGraph& g, const uint32_t* 
     return false;
 }
 
-__global__ void k_prune(DevGraph g, const PruneJob* __restrict__ jobs, int njobs) {
+__global__ void k_prune(DevGraph g, const PruneJob* __restrict__ jobs, int njobs, HubQueue hq) {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
     for (int j = 0; j < njobs; j++) {
@@ -263,8 +286,12 @@ __global__ void k_prune(DevGraph g, const PruneJob* __restrict__ jobs, int njobs
                     e0 = off[v];
                     e1 = off[v + 1];
                 }
-                const bool is_long = keep && e1 - e0 > SHORT_LIST;
-                if (keep && !is_long) keep = any_hit_serial(g, adj, e0, e1, J.con_lab[c], J.con_bm[c]);
+                // a hub's constraint is decided by a block later (it clears the bit
+                // when nothing hits); the other constraints go on here
+                const bool queued = hub_push(hq, keep && e1 - e0 > HUB_LIST,
+                                             ((unsigned long long)j << 40) | ((unsigned long long)c << 32) | a, lane);
+                const bool is_long = keep && !queued && e1 - e0 > SHORT_LIST;
+                if (keep && !queued && !is_long) keep = any_hit_serial(g, adj, e0, e1, J.con_lab[c], J.con_bm[c]);
                 for (uint32_t lm = __ballot_sync(0xffffffffu, is_long); lm; lm &= lm - 1) {
                     const int src = __ffs(lm) - 1;
                     const uint32_t b0 = __shfl_sync(0xffffffffu, e0, src), b1 = __shfl_sync(0xffffffffu, e1, src);
@@ -278,7 +305,7 @@ __global__ void k_prune(DevGraph g, const PruneJob* __restrict__ jobs, int njobs
 }
 
 // off[a] = number of children of parent candidate a
-__global__ void k_cpi_count(DevGraph g, const CpiJob* __restrict__ jobs, int njobs) {
+__global__ void k_cpi_count(DevGraph g, const CpiJob* __restrict__ jobs, int njobs, HubQueue hq) {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
     for (int j = 0; j < njobs; j++) {
@@ -295,6 +322,8 @@ __global__ void k_cpi_count(DevGraph g, const CpiJob* __restrict__ jobs, int njo
                 e0 = off[v];
                 e1 = off[v + 1];
             }
+            const bool queued = hub_push(hq, e1 - e0 > HUB_LIST, ((unsigned long long)j << 40) | a, lane);
+            if (queued) e1 = e0;  // counted by a block later
             const bool is_long = e1 - e0 > SHORT_LIST;
             uint32_t cnt = 0;
             if (!is_long)
@@ -319,7 +348,7 @@ __global__ void k_cpi_count(DevGraph g, const CpiJob* __restrict__ jobs, int njo
                 c = __reduce_add_sync(0xffffffffu, c);
                 if (lane == src) cnt = c;
             }
-            if (a < n) J.off[a] = cnt;
+            if (a < n && !queued) J.off[a] = cnt;
         }
     }
 }
@@ -394,7 +423,7 @@ __global__ void __launch_bounds__(COMPACT_THREADS) k_cpi_scan(const CpiJob* __re
     }
 }
 
-__global__ void k_cpi_fill(DevGraph g, const CpiJob* __restrict__ jobs, int njobs) {
+__global__ void k_cpi_fill(DevGraph g, const CpiJob* __restrict__ jobs, int njobs, HubQueue hq) {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
     for (int j = 0; j < njobs; j++) {
@@ -408,11 +437,14 @@ __global__ void k_cpi_fill(DevGraph g, const CpiJob* __restrict__ jobs, int njob
             uint32_t e0 = 0, e1 = 0, o = 0, oend = 0;
             if (a < n) {
                 const uint32_t v = (uint32_t)J.pcand[a];
-                e0 = off[v];
-                e1 = off[v + 1];
                 o = J.off[a];
                 oend = J.off[a + 1];
+                if (oend > o) {  // a parent without index edges skips its list
+                    e0 = off[v];
+                    e1 = off[v + 1];
+                }
             }
+            if (hub_push(hq, e1 - e0 > HUB_LIST, ((unsigned long long)j << 40) | a, lane)) e1 = e0;
             const bool is_long = e1 - e0 > SHORT_LIST;
             if (!is_long)
                 for (uint32_t e = e0; e < e1; e += UNROLL) {
@@ -460,6 +492,121 @@ __global__ void k_cpi_fill(DevGraph g, const CpiJob* __restrict__ jobs, int njob
                     w += __popc(bal);
                 }
             }
+        }
+    }
+}
+
+// ---- hub lists, one block per queued (job, candidate[, constraint]) item
+
+__global__ void __launch_bounds__(HUB_THREADS) k_scatter_hub(DevGraph g, const ScatterJob* __restrict__ jobs,
+                                                            HubQueue hq) {
+    const uint32_t nq = hub_count(hq);
+    for (uint32_t t = blockIdx.x; t < nq; t += gridDim.x) {
+        const unsigned long long it = hq.item[t];
+        const ScatterJob& J = jobs[it >> 40];
+        const uint32_t v = (uint32_t)J.qcand[(uint32_t)it];
+        const uint32_t* off = J.scan_out ? g.out_off : g.in_off;
+        const uint32_t* adj = J.scan_out ? g.out_adj : g.in_adj;
+        const uint32_t e1 = off[v + 1];
+        for (uint32_t e = off[v] + threadIdx.x; e < e1; e += HUB_THREADS) {
+            const uint32_t p = __ldg(adj + e);
+            const uint32_t x = p >> g.lbits;
+            if (label_ok(J.lab, (int32_t)(p & g.lmask)) && bit_of(J.filter, x))
+                atomicOr(&J.marks[x >> 5], 1u << (x & 31));
+        }
+    }
+}
+
+// A queued prune constraint: the candidate stays only if some neighbour hits.
+__global__ void __launch_bounds__(HUB_THREADS) k_prune_hub(DevGraph g, const PruneJob* __restrict__ jobs,
+                                                          HubQueue hq) {
+    const uint32_t nq = hub_count(hq);
+    for (uint32_t t = blockIdx.x; t < nq; t += gridDim.x) {
+        const unsigned long long it = hq.item[t];
+        const PruneJob& J = jobs[it >> 40];
+        const int c = (int)((it >> 32) & 0xff);
+        const uint32_t v = (uint32_t)J.cand[(uint32_t)it];
+        const uint32_t* off = J.con_dir[c] ? g.out_off : g.in_off;
+        const uint32_t* adj = J.con_dir[c] ? g.out_adj : g.in_adj;
+        const uint32_t e0 = off[v], e1 = off[v + 1];
+        bool found = false;
+        for (uint32_t b = e0; b < e1; b += HUB_THREADS) {  // block-uniform bounds
+            const uint32_t e = b + threadIdx.x;
+            bool hit = false;
+            if (e < e1) {
+                const uint32_t p = __ldg(adj + e);
+                hit = label_ok(J.con_lab[c], (int32_t)(p & g.lmask)) && bit_of(J.con_bm[c], p >> g.lbits);
+            }
+            if (__syncthreads_or(hit)) {
+                found = true;
+                break;
+            }
+        }
+        if (!found && threadIdx.x == 0) atomicAnd(&J.bm[v >> 5], ~(1u << (v & 31)));
+    }
+}
+
+__global__ void __launch_bounds__(HUB_THREADS) k_cpi_count_hub(DevGraph g, const CpiJob* __restrict__ jobs,
+                                                              HubQueue hq) {
+    using Reduce = cub::BlockReduce<uint32_t, HUB_THREADS>;
+    __shared__ typename Reduce::TempStorage tmp;
+    const uint32_t nq = hub_count(hq);
+    for (uint32_t t = blockIdx.x; t < nq; t += gridDim.x) {
+        const unsigned long long it = hq.item[t];
+        const CpiJob& J = jobs[it >> 40];
+        const uint32_t a = (uint32_t)it;
+        const uint32_t v = (uint32_t)J.pcand[a];
+        const uint32_t* off = J.out ? g.out_off : g.in_off;
+        const uint32_t* adj = J.out ? g.out_adj : g.in_adj;
+        const uint32_t e1 = off[v + 1];
+        uint32_t cnt = 0;
+        for (uint32_t e = off[v] + threadIdx.x; e < e1; e += HUB_THREADS) {
+            const uint32_t p = __ldg(adj + e);
+            cnt += label_ok(J.lab, (int32_t)(p & g.lmask)) && bit_of(J.cbm, p >> g.lbits);
+        }
+        const uint32_t total = Reduce(tmp).Sum(cnt);
+        if (threadIdx.x == 0) J.off[a] = total;
+        __syncthreads();  // tmp is reused by the next item
+    }
+}
+
+// Ordered fill of a hub's index edges: tiles of HUB_THREADS entries, a block
+// scan gives each hit its slot after the hits of the earlier tiles.
+__global__ void __launch_bounds__(HUB_THREADS) k_cpi_fill_hub(DevGraph g, const CpiJob* __restrict__ jobs,
+                                                             HubQueue hq) {
+    using Scan = cub::BlockScan<uint32_t, HUB_THREADS>;
+    __shared__ typename Scan::TempStorage tmp;
+    const uint32_t nq = hub_count(hq);
+    for (uint32_t t = blockIdx.x; t < nq; t += gridDim.x) {
+        const unsigned long long it = hq.item[t];
+        const CpiJob& J = jobs[it >> 40];
+        const uint32_t a = (uint32_t)it;
+        const uint32_t v = (uint32_t)J.pcand[a];
+        const uint32_t* off = J.out ? g.out_off : g.in_off;
+        const uint32_t* adj = J.out ? g.out_adj : g.in_adj;
+        const uint32_t e0 = off[v], e1 = off[v + 1];
+        const uint32_t o = J.off[a], oend = J.off[a + 1];
+        uint32_t running = 0;
+        for (uint32_t b = e0; b < e1; b += HUB_THREADS) {  // block-uniform bounds
+            const uint32_t e = b + threadIdx.x;
+            bool hit = false;
+            uint32_t x = 0, word = 0;
+            if (e < e1) {
+                const uint32_t p = __ldg(adj + e);
+                x = p >> g.lbits;
+                word = J.cbm[x >> 5];
+                hit = label_ok(J.lab, (int32_t)(p & g.lmask)) && ((word >> (x & 31)) & 1u);
+            }
+            uint32_t excl, total;
+            Scan(tmp).ExclusiveSum(hit ? 1u : 0u, excl, total);
+            if (hit) {
+                const uint64_t slot = (uint64_t)o + running + excl;
+                if (slot < oend && slot < J.cap)
+                    J.idx[slot] = make_int2((int32_t)(J.crank[x >> 5] + __popc(word & ((1u << (x & 31)) - 1))),
+                                            (int32_t)x);
+            }
+            running += total;
+            __syncthreads();  // tmp is reused by the next tile
         }
     }
 }
@@ -518,15 +665,24 @@ int launch_compact(const DevGraph& g, const CompactJob* d_jobs, int njobs, cudaS
     return check_launch("k_compact");
 }
 
-int launch_scatter(const DevGraph& g, const ScatterJob* d_jobs, int njobs, cudaStream_t st) {
+static int hub_reset(const HubQueue& hq, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(hq.n, 0, sizeof(uint32_t), st);
+    return e == cudaSuccess ? GFD_OK : cuda_fail(e, "hub queue reset");
+}
+
+int launch_scatter(const DevGraph& g, const ScatterJob* d_jobs, int njobs, const HubQueue& hq, cudaStream_t st) {
     if (njobs <= 0) return GFD_OK;
-    k_scatter<<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs);
+    if (int rc = hub_reset(hq, st)) return rc;
+    k_scatter<<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    k_scatter_hub<<<HUB_GRID, HUB_THREADS, 0, st>>>(g, d_jobs, hq);
     return check_launch("k_scatter");
 }
 
-int launch_prune(const DevGraph& g, const PruneJob* d_jobs, int njobs, cudaStream_t st) {
+int launch_prune(const DevGraph& g, const PruneJob* d_jobs, int njobs, const HubQueue& hq, cudaStream_t st) {
     if (njobs <= 0) return GFD_OK;
-    k_prune<<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs);
+    if (int rc = hub_reset(hq, st)) return rc;
+    k_prune<<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    k_prune_hub<<<HUB_GRID, HUB_THREADS, 0, st>>>(g, d_jobs, hq);
     return check_launch("k_prune");
 }
 
@@ -535,9 +691,11 @@ uint32_t cpi_chunks(uint64_t max_parent_candidates) {
 }
 
 int launch_cpi_count(const DevGraph& g, const CpiJob* d_jobs, int njobs, uint32_t nchunks, int32_t* d_err,
-                     uint32_t* d_totals, cudaStream_t st) {
+                     uint32_t* d_totals, const HubQueue& hq, cudaStream_t st) {
     if (njobs <= 0) return GFD_OK;
-    k_cpi_count<<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs);
+    if (int rc = hub_reset(hq, st)) return rc;
+    k_cpi_count<<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    k_cpi_count_hub<<<HUB_GRID, HUB_THREADS, 0, st>>>(g, d_jobs, hq);
     const int grid = (int)std::min<uint64_t>((uint64_t)njobs * nchunks, 152 * 4);
     k_cpi_sums<<<grid, COMPACT_THREADS, 0, st>>>(d_jobs, njobs, nchunks);
     k_cpi_scan<<<grid, COMPACT_THREADS, 0, st>>>(d_jobs, njobs, nchunks, d_err);
@@ -545,9 +703,11 @@ int launch_cpi_count(const DevGraph& g, const CpiJob* d_jobs, int njobs, uint32_
     return check_launch("k_cpi_count");
 }
 
-int launch_cpi_fill(const DevGraph& g, const CpiJob* d_jobs, int njobs, cudaStream_t st) {
+int launch_cpi_fill(const DevGraph& g, const CpiJob* d_jobs, int njobs, const HubQueue& hq, cudaStream_t st) {
     if (njobs <= 0) return GFD_OK;
-    k_cpi_fill<<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs);
+    if (int rc = hub_reset(hq, st)) return rc;
+    k_cpi_fill<<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    k_cpi_fill_hub<<<HUB_GRID, HUB_THREADS, 0, st>>>(g, d_jobs, hq);
     return check_launch("k_cpi_fill");
 }
 

@@ -220,6 +220,7 @@ struct Group {
     };
     std::vector<Off> offs;
     size_t o_keybm = 0, o_keys = 0, o_tmp = 0, o_cmp_sums = 0, o_cpi_sums = 0, o_cpi_tot = 0;
+    size_t o_hubq = 0, o_hubn = 0;  // hub queue of the adjacency kernels
     uint8_t* cpi_base = nullptr;  // index edges, sized after counting
     size_t cpi_bytes = 0;
     size_t cpi_bound = 0;  // upper bound of cpi_bytes known at planning time
@@ -367,6 +368,8 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
     G->o_cmp_sums = L.take(4ull * G->cmp_chunks * std::max<size_t>(1, n_compact));
     G->o_cpi_sums = L.take(8ull * G->cpi_nch * std::max<size_t>(1, n_cpi));
     G->o_cpi_tot = L.take(4ull * std::max<size_t>(1, n_cpi));
+    G->o_hubq = L.take(8ull * HUB_CAP);
+    G->o_hubn = L.take(4);
     // the region uploaded from the host: keys and job tables
     G->o_jobs = L.size;
     G->o_keys = L.take(sizeof(FilterKey) * std::max(1, nkeys));
@@ -606,6 +609,7 @@ int group_launch(gfd_graph* g, Group* G, const Tables& T, cudaMemPool_t pool, cu
                  int64_t* launches) {
     const DevGraph& dg = g->dg;
     uint8_t* base = G->base;
+    const HubQueue hq{(unsigned long long*)(base + G->o_hubq), (uint32_t*)(base + G->o_hubn), HUB_CAP};
     prof.begin(PROF_FILTER, st);
     if (int rc = launch_filter(dg, (const FilterKey*)(base + G->o_keys), (int)G->keys.size(),
                                (uint32_t*)(base + G->o_keybm), st))
@@ -621,9 +625,11 @@ int group_launch(gfd_graph* g, Group* G, const Tables& T, cudaMemPool_t pool, cu
                 rc = launch_compact(dg, (const CompactJob*)(base + G->o_cmp) + ph.first, (int)ph.count, st);
                 break;
             case 2:
-                rc = launch_scatter(dg, (const ScatterJob*)(base + G->o_sct) + ph.first, (int)ph.count, st);
+                rc = launch_scatter(dg, (const ScatterJob*)(base + G->o_sct) + ph.first, (int)ph.count, hq, st);
                 break;
-            case 3: rc = launch_prune(dg, (const PruneJob*)(base + G->o_prn) + ph.first, (int)ph.count, st); break;
+            case 3:
+                rc = launch_prune(dg, (const PruneJob*)(base + G->o_prn) + ph.first, (int)ph.count, hq, st);
+                break;
             case 4: {
                 cudaError_t e = cudaMemsetAsync(base + G->o_tmp, 0, 4ull * dg.nwords * ph.count, st);
                 rc = e == cudaSuccess ? GFD_OK : cuda_fail(e, "cudaMemsetAsync");
@@ -631,7 +637,7 @@ int group_launch(gfd_graph* g, Group* G, const Tables& T, cudaMemPool_t pool, cu
             }
         }
         if (rc) return rc;
-        launches[PROF_REFINE] += ph.kind == 4 ? 0 : (ph.kind == 1 ? 2 : 1);
+        launches[PROF_REFINE] += ph.kind == 4 ? 0 : (ph.kind == 0 ? 1 : 2);  // scatter/prune: + hub kernel
     }
     prof.end(PROF_REFINE, st);
     prof.begin(PROF_INDEX, st);
@@ -639,7 +645,7 @@ int group_launch(gfd_graph* g, Group* G, const Tables& T, cudaMemPool_t pool, cu
     if (ncpi) {
         CpiJob* d_cpi = (CpiJob*)(base + G->o_cpi);
         uint32_t* d_tot = (uint32_t*)(base + G->o_cpi_tot);
-        if (int rc = launch_cpi_count(dg, d_cpi, ncpi, G->cpi_nch, T.err, d_tot, st)) return rc;
+        if (int rc = launch_cpi_count(dg, d_cpi, ncpi, G->cpi_nch, T.err, d_tot, hq, st)) return rc;
         // size the index edges exactly: one read-back of the per-edge totals
         std::vector<uint32_t> tot(ncpi);
         GFD_CUDA(cudaMemcpyAsync(tot.data(), d_tot, 4ull * ncpi, cudaMemcpyDeviceToHost, st));
@@ -668,8 +674,8 @@ int group_launch(gfd_graph* g, Group* G, const Tables& T, cudaMemPool_t pool, cu
         for (int s = 0; s < G->n; s++)
             GFD_CUDA(cudaMemcpyAsync(&T.desc[G->slot[s]].cpi_idx, G->descs[s].cpi_idx, sizeof(G->descs[s].cpi_idx),
                                      cudaMemcpyHostToDevice, st));
-        if (int rc = launch_cpi_fill(dg, d_cpi, ncpi, st)) return rc;
-        launches[PROF_INDEX] += 5;
+        if (int rc = launch_cpi_fill(dg, d_cpi, ncpi, hq, st)) return rc;
+        launches[PROF_INDEX] += 7;
     }
     prof.end(PROF_INDEX, st);
     return GFD_OK;
