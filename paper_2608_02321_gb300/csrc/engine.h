@@ -106,7 +106,7 @@ struct CpiJob {          // index edges of one spanning-tree edge
 // distribution) are queued by the warp kernels and scanned afterwards by whole
 // blocks, so that one hub does not leave a single warp running long after the
 // rest of the launch; a full queue leaves the list to its warp.
-constexpr uint32_t HUB_LIST = 4096;
+constexpr uint32_t HUB_LIST = 1024;
 constexpr uint32_t HUB_CAP = 1u << 19;
 struct HubQueue {
     unsigned long long* item;  // (job << 40) | (constraint << 32) | candidate index

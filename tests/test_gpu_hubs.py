@@ -1,4 +1,4 @@
-"""Hubs: adjacency lists longer than the warp kernels keep (they are queued and
+"""Hubs: adjacency lists longer than the warp kernels keep (over 1024 entries) (they are queued and
 scanned by whole blocks in refinement and index construction). Closed forms on
 stars of 20,000 leaves, and graphs with planted out- and in-hubs of degree 6,000
 compared with the oracle in both matching modes and with X pushed down."""
