@@ -151,7 +151,9 @@ typedef struct {
 
 /* Tuning options; a NULL gfd_opts* or zero fields select the defaults. */
 typedef struct {
-    int64_t frontier_budget_bytes; /* device bytes for partial-match buffers */
+    int64_t frontier_budget_bytes; /* device bytes for partial-match buffers
+                                      (0: the tuned choice, else min(128 GiB,
+                                      half the free device memory)) */
     int32_t chunk_rows;            /* partial matches expanded per step and GFD */
     int32_t kernel_variant;        /* enumeration kernel: 0 = the graph's tuned
                                       choice (gfd_autotune) or the default;
