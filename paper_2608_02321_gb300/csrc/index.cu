@@ -1,15 +1,19 @@
 // Compact path index construction (Section III.B, step 1).
 //
-//   k_filter   step 1a-1b: candidates by label and degree (and self-loop),
-//              one coalesced pass over vertex data for all filter keys;
-//   k_scatter  step 1c, top-down: mark vertices adjacent (in the direction and
-//   k_and      with the label of a pattern edge) to the candidates of an
-//              earlier level, then intersect;
-//   k_prune    step 1c, bottom-up: remove dead ends, i.e. candidates with no
-//              neighbour among the candidates of a later level;
+//   k_filter   step 1a-1b: candidates by label and degree (and self-loop, and
+//              pushed-down constant X literals), one coalesced pass over vertex
+//              data for all filter keys;
+//   k_scatter  step 1c: mark vertices adjacent (in the direction and with the
+//   k_and      label of a pattern edge) to the candidates of another level,
+//              then intersect;
+//   k_prune    step 1c: remove candidates with no such neighbour among the
+//              candidates of another level (early exit at the first one);
+//              top-down and bottom-up use whichever of the two is cheaper;
 //   k_compact  bitmap -> exclusive popcount prefix (O(1) rank) + sorted list;
 //   k_cpi_*    step 1d: for each spanning-tree edge, the index edges from
-//              every parent candidate to the positions of its child candidates.
+//              every parent candidate to the positions of its child candidates;
+//   *_hub      the same for adjacency lists over HUB_LIST entries, one block
+//              per list (queued by the warp kernels).
 //
 // Every launch processes a table of jobs; blocks (or warps) stride over the
 // items of each job with a per-job rotation so that small jobs spread out.
@@ -150,8 +154,9 @@ __global__ void __launch_bounds__(COMPACT_THREADS) k_compact_write(DevGraph g, c
 
 // The adjacency kernels below give each lane of a warp one candidate and let
 // the lane scan a short list alone; lists longer than SHORT_LIST are left to
-// the whole warp, one after the other (ballot of the long ones), so hubs are
-// scanned 32 edges at a time without idling lanes on short lists.
+// the whole warp, one after the other (ballot of the long ones), scanned 32
+// entries at a time without idling lanes on short lists; hub lists (over
+// HUB_LIST entries) are queued for a block each.
 constexpr uint32_t SHORT_LIST = 32;
 
 // A lane scanning a short list alone reads UNROLL entries per round and then
