@@ -845,6 +845,7 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
         GFD_CUDA(cudaMemcpyAsync(T.vptr, vbuf.data(), sizeof(int32_t*) * n, cudaMemcpyHostToDevice, st));
         GFD_CUDA(cudaMemsetAsync(T.vcur, 0, 8ull * n, st));
         if (int rc = launch_split(T.desc, T.varena, hs.varena_used, T.vstride, T.vptr, T.vcur, st)) return rc;
+        launches[PROF_ENUM] += 1;  // the split belongs to the enumeration's output
     }
     for (int s = 0; s < n; s++) {
         gfd_result* r = make_result(G.plans[s], states[s], hs.steps, hs.probes, vbuf[s], st);
