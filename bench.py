@@ -159,6 +159,12 @@ def oracle_sample(g, qs, seconds: float, threads: int, seed: int = 7):
     return sum(r[0] for r in res), wall, sum(r[1] for r in res)
 
 
+def workload_config(desc: str, n_gpus: int) -> dict:
+    """The `config` of a bench line (the same for the GPU and the reference arm)."""
+    return {"workload": desc, "l2": "inputs larger than L2 and a 512 MB L2 flush before every timed step",
+            "parallelism": "replicas" if n_gpus > 1 else "single GPU"}
+
+
 def cpu_threads() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -185,7 +191,7 @@ def run_reference(args, g, qs, desc):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic", "config": {"workload": desc, "parallelism": "replicas"},
+            "data": "synthetic", "config": workload_config(desc, args.gpus),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -509,9 +515,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-                "config": {"workload": desc, "l2": "inputs larger than L2 and a 512 MB L2 flush before "
-                                                  "every timed step",
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "config": workload_config(desc, world),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "plain": plain, "non_induced": non_induced, "push_x": push_x, "disconnected": disconnected, "serving": serving, "autotuned": tuned,
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,
