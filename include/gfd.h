@@ -222,6 +222,13 @@ const int32_t *gfd_result_tuples(gfd_result *r);
  * result's buffer). Returns GFD_OK, GFD_ERR_INVALID_ARG (NULL or too small a
  * buffer), GFD_ERR_OUT_OF_MEMORY or a CUDA error code. */
 int gfd_result_copy_tuples(gfd_result *r, int32_t *out, uint64_t capacity);
+/* The sorted tuples of n results (say, one gfd_validate_batch) written back to
+ * back into caller-owned host memory `out` of `capacity` int32: result 0's
+ * n_violations * k ints, then result 1's, and so on. One device sort over all of
+ * them (keyed by result, then tuple) and one copy, instead of one per result.
+ * Returns GFD_OK, GFD_ERR_INVALID_ARG (NULL arguments or too small a buffer),
+ * GFD_ERR_OUT_OF_MEMORY or a CUDA error code. */
+int gfd_results_copy_tuples(gfd_result *const *rs, int32_t n, int32_t *out, uint64_t capacity);
 /* Device time in milliseconds spent in kernel class `which` (0 candidate
  * filter, 1 refinement, 2 index build, 3 enumeration, 4 result sort) and the
  * number of launches, when GFD_FLAG_PROFILE was set; else 0. */

@@ -86,6 +86,7 @@ _SIGS = {
     "gfd_result_arity": (C.c_int32, [C.c_void_p]),
     "gfd_result_tuples": (C.c_void_p, [C.c_void_p]),
     "gfd_result_copy_tuples": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64]),
+    "gfd_results_copy_tuples": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_uint64]),
     "gfd_result_profile": (C.c_double, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
     "gfd_result_stat": (C.c_uint64, [C.c_void_p, C.c_int32]),
     "gfd_result_free": (None, [C.c_void_p]),
@@ -359,6 +360,22 @@ def node_candidates_noalloc(g: Graph, gfd, node: int, out_ptr: int, out_cap: int
 
 def graph_load(graph, stream=None, with_reverse: bool = False) -> Graph:
     return Graph(graph, stream, with_reverse)
+
+
+def violations_all(results) -> list:
+    """The sorted violation lists of several results ([n_i, k_i] int32 each),
+    fetched with one device sort and one copy (gfd_results_copy_tuples)."""
+    results = list(results)
+    sizes = [r.n_violations * r.k for r in results]
+    buf = np.empty(max(1, sum(sizes)), dtype=np.int32)
+    hs = (C.c_void_p * max(1, len(results)))(*[r._h for r in results])
+    _check(_lib.gfd_results_copy_tuples(hs, len(results), buf.ctypes.data_as(C.c_void_p),
+                                        C.c_uint64(sum(sizes))))
+    out, at = [], 0
+    for r, sz in zip(results, sizes):
+        out.append(buf[at:at + sz].reshape(r.n_violations, r.k))
+        at += sz
+    return out
 
 
 def validate(g: Graph, gfd, **opts) -> Result:

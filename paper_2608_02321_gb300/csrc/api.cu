@@ -87,6 +87,26 @@ const int32_t* gfd_result_tuples(gfd_result* r) {
     return r->tuples.get();
 }
 
+int gfd_results_copy_tuples(gfd_result* const* rs, int32_t n, int32_t* out, uint64_t capacity) {
+    if (n < 0 || (n > 0 && !rs)) {
+        gfd::set_error(GFD_ERR_INVALID_ARG, "gfd_results_copy_tuples: NULL results or negative count");
+        return GFD_ERR_INVALID_ARG;
+    }
+    uint64_t need = 0;
+    for (int32_t i = 0; i < n; i++) {
+        if (!rs[i]) {
+            gfd::set_error(GFD_ERR_INVALID_ARG, "gfd_results_copy_tuples: result %d is NULL", i);
+            return GFD_ERR_INVALID_ARG;
+        }
+        need += rs[i]->n_viol * (uint64_t)rs[i]->k;
+    }
+    if (need > 0 && !out) {
+        gfd::set_error(GFD_ERR_INVALID_ARG, "gfd_results_copy_tuples: NULL output");
+        return GFD_ERR_INVALID_ARG;
+    }
+    return gfd::results_sort_copy(rs, n, out, capacity);
+}
+
 int gfd_result_copy_tuples(gfd_result* r, int32_t* out, uint64_t capacity) {
     if (!r || (!out && r->n_viol > 0)) {
         gfd::set_error(GFD_ERR_INVALID_ARG, "gfd_result_copy_tuples: NULL argument");

@@ -174,6 +174,9 @@ int autotune(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opts
 // Sort the violation tuples on the device and copy them to dst (host memory,
 // n_viol * k ints); result_fetch does this into the result's own buffer.
 int result_sort_copy(gfd_result* r, int32_t* dst);
+// The same for n results at once, into one host buffer: result 0's tuples,
+// then result 1's, ... (one device sort keyed by (result, tuple), one copy).
+int results_sort_copy(gfd_result* const* rs, int n, int32_t* out, uint64_t capacity);
 int result_fetch(gfd_result* r);
 
 }  // namespace gfd

@@ -1217,6 +1217,44 @@ __global__ void k_gather_rows(const int32_t* t, int k, const uint32_t* perm, uin
     }
 }
 
+// Several results' violation lists sorted together: rows of a matrix of
+// width W = 1 + max k, column 0 the result's index (most significant), the
+// tuple after it (zero-padded; only rows of the same result are ever compared
+// past column 0).
+struct PackSrc {
+    const int32_t* p;   // the result's unsorted tuples
+    int32_t k;
+    int32_t pad;
+    uint64_t row_off;   // first row of the result in the matrix (and in sorted order)
+    uint64_t int_off;   // first int of the result in the packed output
+};
+
+__global__ void k_pack_multi(const PackSrc* src, int nres, uint64_t total, int W, int32_t* M) {
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < total; g += (uint64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nres;  // src[lo].row_off <= g < src[hi].row_off (src[nres] = total)
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (src[mid].row_off <= g) lo = mid;
+            else hi = mid;
+        }
+        const PackSrc s = src[lo];
+        const uint64_t local = g - s.row_off;
+        int32_t* row = M + g * W;
+        row[0] = lo;
+        for (int c = 0; c < W - 1; c++) row[1 + c] = c < s.k ? s.p[local * s.k + c] : 0;
+    }
+}
+
+__global__ void k_unpack_multi(const PackSrc* src, const int32_t* M, int W, const uint32_t* perm, uint64_t total,
+                               int32_t* out) {
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < total; p += (uint64_t)gridDim.x * blockDim.x) {
+        const int32_t* row = M + (uint64_t)perm[p] * W;
+        const PackSrc s = src[row[0]];
+        int32_t* dst = out + s.int_off + (p - s.row_off) * s.k;
+        for (int c = 0; c < s.k; c++) dst[c] = row[1 + c];
+    }
+}
+
 }  // namespace
 
 // Lexicographic order of the violation tuples (Vio is a set; this fixes a
@@ -1283,6 +1321,79 @@ int result_sort_copy(gfd_result* r, int32_t* dst) {
     cudaFreeAsync(k0, st);
     cudaFreeAsync(k1, st);
     cudaFreeAsync(sorted, st);
+    return rc;
+}
+
+int results_sort_copy(gfd_result* const* rs, int n, int32_t* out, uint64_t capacity) {
+    std::vector<PackSrc> src((size_t)n + 1);
+    uint64_t total = 0, ints = 0;
+    int kmax = 1;
+    cudaStream_t st = nullptr;
+    for (int r = 0; r < n; r++) {
+        src[r] = PackSrc{rs[r]->d_viol, rs[r]->k, 0, total, ints};
+        total += rs[r]->n_viol;
+        ints += rs[r]->n_viol * (uint64_t)rs[r]->k;
+        kmax = std::max(kmax, rs[r]->k);
+        if (rs[r]->n_viol && !st) st = rs[r]->stream;
+    }
+    src[n] = PackSrc{nullptr, 1, 0, total, ints};
+    if (capacity < ints) {
+        set_error(GFD_ERR_INVALID_ARG, "gfd_results_copy_tuples: capacity %llu < %llu ints",
+                  (unsigned long long)capacity, (unsigned long long)ints);
+        return GFD_ERR_INVALID_ARG;
+    }
+    if (total == 0) return GFD_OK;
+    if (total >= ((uint64_t)1 << 32)) {  // the carried permutation is 32-bit: one result at a time
+        for (int r = 0; r < n; r++)
+            if (int rc = result_sort_copy(rs[r], out + src[r].int_off)) return rc;
+        return GFD_OK;
+    }
+    const int W = kmax + 1;
+    PackSrc* d_src;
+    uint32_t *p0, *p1;
+    uint64_t *k0, *k1;
+    int32_t *M, *dout;
+    GFD_CUDA(cudaMallocAsync((void**)&d_src, sizeof(PackSrc) * ((size_t)n + 1), st));
+    GFD_CUDA(cudaMallocAsync((void**)&M, 4ull * total * W, st));
+    GFD_CUDA(cudaMallocAsync((void**)&p0, 4 * total, st));
+    GFD_CUDA(cudaMallocAsync((void**)&p1, 4 * total, st));
+    GFD_CUDA(cudaMallocAsync((void**)&k0, 8 * total, st));
+    GFD_CUDA(cudaMallocAsync((void**)&k1, 8 * total, st));
+    GFD_CUDA(cudaMallocAsync((void**)&dout, 4 * ints, st));
+    GFD_CUDA(cudaMemcpyAsync(d_src, src.data(), sizeof(PackSrc) * ((size_t)n + 1), cudaMemcpyHostToDevice, st));
+    const int grid = (int)std::min<uint64_t>((total + 255) / 256, 152 * 16);
+    k_pack_multi<<<grid, 256, 0, st>>>(d_src, n, total, W, M);
+    k_iota<<<grid, 256, 0, st>>>(p0, total);
+    size_t tb = 0;
+    cub::DoubleBuffer<uint64_t> kb(k0, k1);
+    cub::DoubleBuffer<uint32_t> pb(p0, p1);
+    GFD_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, kb, pb, (int64_t)total, 0, 64, st));
+    void* tmp;
+    GFD_CUDA(cudaMallocAsync(&tmp, tb, st));
+    int rc = GFD_OK;
+    for (int c1 = W - 1; c1 >= 0; c1 -= 2) {  // least significant pair of columns first
+        const int c0 = c1 - 1;
+        k_gather_key<<<grid, 256, 0, st>>>(M, W, pb.Current(), total, c0, c1, kb.Current());
+        cudaError_t e = cub::DeviceRadixSort::SortPairs(tmp, tb, kb, pb, (int64_t)total, 0, c0 >= 0 ? 64 : 32, st);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "cub::DeviceRadixSort::SortPairs");
+            break;
+        }
+    }
+    if (rc == GFD_OK) {
+        k_unpack_multi<<<grid, 256, 0, st>>>(d_src, M, W, pb.Current(), total, dout);
+        cudaError_t e = cudaMemcpyAsync(out, dout, 4 * ints, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "violation copy");
+    }
+    cudaFreeAsync(tmp, st);
+    cudaFreeAsync(d_src, st);
+    cudaFreeAsync(M, st);
+    cudaFreeAsync(p0, st);
+    cudaFreeAsync(p1, st);
+    cudaFreeAsync(k0, st);
+    cudaFreeAsync(k1, st);
+    cudaFreeAsync(dout, st);
     return rc;
 }
 

@@ -222,3 +222,23 @@ def test_kernel_variants_and_autotune(lib, oracle_mod):
     res = dg.validate_batch(qs)
     for i, r in enumerate(res):
         assert_same((r.n_matches, r.violations()), want[i], f"tuned gfd {i}")
+
+
+def test_batched_violation_fetch(lib, oracle_mod):
+    """gfd_results_copy_tuples: one sort and one copy for many results gives
+    each result's own sorted list, also across two calls and with empty lists."""
+    g, qs = configs.batched(scale=400, n_gfds=24)
+    dg = gpu_graph(g)
+    res = dg.validate_batch(qs[:16])
+    more = [dg.validate(q) for q in qs[16:]]
+    allr = res + more
+    got = G.violations_all(allr)
+    assert len(got) == len(allr)
+    empty = 0
+    for i, r in enumerate(allr):
+        assert_same((r.n_matches, got[i]), (r.n_matches, r.violations()), f"result {i}")
+        empty += r.n_violations == 0
+    for i in (0, 3, 17):
+        assert_same((allr[i].n_matches, got[i]), oracle_mod.validate(g, qs[i], threads=os.cpu_count() or 8),
+                    f"oracle {i}")
+    assert G.violations_all([]) == []
