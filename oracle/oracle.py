@@ -201,6 +201,35 @@ def count_within(og: OracleGraph, gfd, roots, seconds: float, induced: bool = Tr
     return int(nm.value), int(done.value)
 
 
+def validate_within(og: OracleGraph, gfd, roots, seconds: float, induced: bool = True):
+    """(matches, sorted violations, roots searched to the end) for the given
+    roots, stopping after about `seconds`: the matches and violations are those
+    of roots[:done] exactly (the root in progress at the deadline is dropped)."""
+    lib = og._lib
+    s, keep = _gfd_struct(gfd)
+    nm = C.c_uint64(0)
+    vp = C.c_void_p(None)
+    nv = C.c_int64(0)
+    done = C.c_int64(0)
+    r = np.ascontiguousarray(roots, dtype=np.int32)
+    rc = lib.og_validate_mode(og._h, C.byref(s), 1 if induced else 0, _ptr(r), int(r.shape[0]),
+                              float(seconds), C.byref(nm), C.byref(vp), C.byref(nv), C.byref(done), None)
+    if rc != 0:
+        if vp.value:
+            lib.og_free(vp)
+        raise ValueError("oracle rejected the GFD (malformed pattern)")
+    k = gfd.k
+    n = int(nv.value)
+    out = np.zeros((0, k), dtype=np.int32)
+    if n:
+        buf = (C.c_int32 * (n * k)).from_address(vp.value)
+        out = np.frombuffer(buf, dtype=np.int32).reshape(n, k).copy()
+    if vp.value:
+        lib.og_free(vp)
+    del keep
+    return int(nm.value), sort_tuples(out), int(done.value)
+
+
 def sort_tuples(t: np.ndarray) -> np.ndarray:
     """Lexicographic row order (library sort as a step)."""
     if t.shape[0] <= 1:
