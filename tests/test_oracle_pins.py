@@ -211,3 +211,20 @@ def test_rejects_bad_inputs(oracle_mod):
         _v(oracle_mod, g, GFD([0, 0], [(0, 1, 0)], [Literal.const(0, 9, 1)]))  # bad attribute
     with pytest.raises(ValueError):
         edges_graph(2, [(0, 1, 0), (0, 1, 1)])               # repeated pair
+
+
+def test_validate_within_is_a_root_prefix(oracle_mod):
+    """The deadline-bounded oracle returns exactly the result of the roots it
+    finished: with room for all roots it equals the unbounded run, and what it
+    returns under a short deadline equals the unbounded run on roots[:done]."""
+    for seed in range(20):
+        g, q = random_case(seed)
+        og = oracle_mod.OracleGraph(g)
+        roots = np.arange(g.n_vertices, dtype=np.int32)
+        nm, v, done = oracle_mod.validate_within(og, q, roots, 60.0)
+        assert done == g.n_vertices
+        assert (nm, v.tolist()) == (lambda r: (r[0], r[1].tolist()))(oracle_mod.validate(og, q))
+        nm2, v2, done2 = oracle_mod.validate_within(og, q, roots, 1e-9)
+        want = oracle_mod.validate(og, q, roots=roots[:done2]) if done2 else (0, np.zeros((0, q.k), np.int32))
+        assert nm2 == want[0]
+        np.testing.assert_array_equal(v2, want[1])
