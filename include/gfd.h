@@ -252,7 +252,9 @@ void gfd_result_free(gfd_result *r);
  * requests admitted later overlap on the device with those already running.
  * Requests that finish in that round are moved to the result queue, read with
  * gfd_session_next_result in completion order. The graph stays resident and
- * the session's slot tables are reused across requests.
+ * the session's slot tables are reused across requests. opts->flags apply to
+ * every request of the session (GFD_FLAG_NON_INDUCED, GFD_FLAG_PUSH_X);
+ * disconnected patterns are admitted like any other.
  */
 int gfd_session_create(const gfd_graph *g, int32_t max_slots, const gfd_opts *opts,
                        gfd_session **out);
