@@ -213,9 +213,11 @@ def aggregate(step_ms: float, matches: int, dist=None, device: str = "cpu"):
 
 
 # ------------------------------------------------------------------ GPU arm
-def kernel_traffic():
-    """dram bytes per launch of the enumeration kernel from the committed ncu
-    summary, if it was taken on the current source of that kernel."""
+def kernel_traffic(work_items: int):
+    """DRAM bytes of one enumeration launch: the traffic per work item of the
+    committed small-case ncu capture (one kernel, one launch, a few GB on the
+    device) times this launch's work items, if the capture was taken on the
+    current source of that kernel; else None."""
     try:
         text = open(PROFILE_NOTE).read()
     except OSError:
@@ -224,11 +226,11 @@ def kernel_traffic():
     t = None
     s = None
     for ln in text.splitlines():
-        if ln.startswith("traffic_bytes_per_launch:"):
+        if ln.startswith("traffic_bytes_per_work_item:"):
             t = float(ln.split(":", 1)[1].split()[0])
         if ln.startswith("source_sha256_16:"):
             s = ln.split(":", 1)[1].strip()
-    return t if (t is not None and s == sha) else None
+    return t * work_items if (t is not None and s == sha) else None
 
 
 def main():
@@ -351,7 +353,8 @@ def main():
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = b_alg / t_enum / 1e9 if t_enum > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if peak else None, "traffic": kernel_traffic(),
+                "frac": achieved / peak if peak else None, "traffic": kernel_traffic(work),
+                "traffic_source": "ncu DRAM bytes per work item of a small capture x this launch's work items",
                 "kernel": "k_persistent (enumeration)", "launch_ms": t_enum * 1000,
                 "alg_bytes_per_launch": b_alg,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}

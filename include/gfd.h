@@ -173,7 +173,9 @@ typedef struct {
  * reverse CSR consistency) and keep it resident. *out is set on GFD_OK. */
 int gfd_graph_load(const gfd_graph_desc *desc, const gfd_opts *opts, gfd_graph **out);
 
-/* Release a graph handle and its device memory. */
+/* Release a graph handle and its device memory (the graph G of Section II
+ * loaded by gfd_graph_load). Waits for work still running on the graph's
+ * stream; NULL is a no-op. */
 void gfd_graph_free(gfd_graph *g);
 
 /* Autotuner: validate the batch phis[0..n) once per enumeration-kernel variant,
@@ -186,7 +188,8 @@ void gfd_graph_free(gfd_graph *g);
 int gfd_autotune(gfd_graph *g, const gfd_gfd *const *phis, int32_t n, const gfd_opts *opts,
                  gfd_opts *best);
 
-/* Vertex count, edge count and resident device bytes of a loaded graph. */
+/* |V|, |E| (Section II, G = (V, E, L, F_A)) and the resident device bytes of
+ * a loaded graph; 0 for NULL. */
 int32_t gfd_graph_vertices(const gfd_graph *g);
 int64_t gfd_graph_edges(const gfd_graph *g);
 int64_t gfd_graph_device_bytes(const gfd_graph *g);
@@ -204,11 +207,14 @@ int gfd_validate(const gfd_graph *g, const gfd_gfd *phi, const gfd_opts *opts,
 int gfd_validate_batch(const gfd_graph *g, const gfd_gfd *const *phis, int32_t n,
                        const gfd_opts *opts, gfd_result **out);
 
-/* Number of matches of Q (all of them, whether or not they satisfy X). */
+/* Number of matches h of Q in G (Section II, "match": all of them, whether or
+ * not h satisfies X; with GFD_FLAG_PUSH_X only those that satisfy X). 0 for
+ * NULL. */
 uint64_t gfd_result_matches(const gfd_result *r);
-/* Number of violations |Vio({φ}, G)|. */
+/* Number of violations |Vio({φ}, G)| (Section II: matches that satisfy X and
+ * not Y, or satisfy X when Y is false). 0 for NULL. */
 uint64_t gfd_result_violations(const gfd_result *r);
-/* k, the length of each violation tuple. */
+/* k = |x̄|, the length of each violation tuple h(x̄) (Section II). 0 for NULL. */
 int32_t gfd_result_arity(const gfd_result *r);
 /* The violations as [n_violations][k] int32 tuples (h(x_0), ..., h(x_{k-1})),
  * sorted lexicographically; host memory owned by the result. The sort and the
@@ -226,6 +232,8 @@ int gfd_result_copy_tuples(gfd_result *r, int32_t *out, uint64_t capacity);
  * back into caller-owned host memory `out` of `capacity` int32: result 0's
  * n_violations * k ints, then result 1's, and so on. One device sort over all of
  * them (keyed by result, then tuple) and one copy, instead of one per result.
+ * The results may come from calls on different streams: the sort runs on the
+ * stream of the first result with violations and waits for the others' streams.
  * Returns GFD_OK, GFD_ERR_INVALID_ARG (NULL arguments or too small a buffer),
  * GFD_ERR_OUT_OF_MEMORY or a CUDA error code. */
 int gfd_results_copy_tuples(gfd_result *const *rs, int32_t n, int32_t *out, uint64_t capacity);
@@ -238,7 +246,7 @@ double gfd_result_profile(const gfd_result *r, int32_t which, int64_t *launches)
  * (sum over pattern nodes), 5 index entries, 6 number of extra runs made
  * because the violations of the call outgrew max_violations_hint. */
 uint64_t gfd_result_stat(const gfd_result *r, int32_t which);
-/* Release a result. */
+/* Release a result and its device and host buffers; NULL is a no-op. */
 void gfd_result_free(gfd_result *r);
 
 /*
@@ -275,24 +283,31 @@ void gfd_session_free(gfd_session *s);
 /* Candidate filter of pattern node `node` of phi (its label, its out- and
  * in-degree in Q as lower bounds on the data vertex's degrees without
  * self-loops, and its self-loop), written to the caller's DEVICE buffer d_out as
- * increasing vertex ids; *n_out (host) receives how many there are. It
- * allocates no device memory, for callers that must not: code running while a
- * stream is captured into a CUDA graph, servers whose device memory belongs to
- * another allocator or a fixed budget, threads that cannot take the
- * device-wide synchronisation of cudaMalloc/cudaFree. The paper has no
- * counterpart; the same filter runs inside gfd_validate. Its only scratch is a
- * fixed 64 KiB array inside the library, so graphs are limited to 2^26
- * vertices (GFD_ERR_UNSUPPORTED beyond). The first call on each device looks
- * that array up (make it before any stream capture). All calls share the
- * array: calls that overlap on the GPU race, so serialize them (one stream, or
+ * increasing vertex ids; *n_out (host) receives how many there are.
+ * The paper has no counterpart: this is an extra entry point for callers that
+ * may not allocate device memory themselves or through a library. Examples are
+ * a server whose device memory is handed out by its own allocator or reserved
+ * up front under a fixed budget (an allocation by the library would bypass that
+ * accounting, or fail once the reservation holds the free memory), and
+ * latency-bound threads that cannot wait for cudaFree, which synchronises the
+ * whole device. The same filter runs inside gfd_validate.
+ * It allocates nothing: its only scratch is a fixed 64 KiB array inside the
+ * library, which every GPU that loads the library keeps until the process
+ * exits. Graphs are therefore limited to 2^26 vertices (GFD_ERR_UNSUPPORTED
+ * beyond). The first call on each device looks up that array's device address
+ * and the multiprocessor count; make that first call before any stream
+ * capture. All calls share the array and each call clears it before use:
+ * calls that overlap on the GPU race on it, so serialise them (one stream, or
  * wait for the previous call). out_cap is the capacity of d_out in elements;
  * more candidates than that give GFD_ERR_OVERFLOW with *n_out set. The call
- * waits for its own work on cuda_stream (NULL: the graph's stream). */
+ * copies the count to the host and waits for its own work on cuda_stream
+ * (NULL: the graph's stream) before returning. */
 int gfd_node_candidates_noalloc(const gfd_graph *g, const gfd_gfd *phi, int32_t node,
                                 int32_t *d_out, int64_t out_cap, int64_t *n_out,
                                 void *cuda_stream);
 
-/* Message for the calling thread's last non-OK return ("" if none). */
+/* Message for the calling thread's last non-OK return ("" if none); the
+ * library owns the string, valid until the thread's next failing call. */
 const char *gfd_last_error(void);
 
 #ifdef __cplusplus

@@ -237,7 +237,10 @@ class Result:
 class Graph:
     """A graph resident on the GPU (gfd_graph_load)."""
 
-    def __init__(self, graph, stream=None, with_reverse: bool = False):
+    def __init__(self, graph, stream=None, reverse=None):
+        """graph: CSR arrays (out_off, out_dst, out_elabel, vlabel, attrs).
+        reverse: None (the library builds the reverse CSR) or the caller's
+        (in_off, in_src, in_elabel), which must describe the same edge set."""
         lib = load_library()
         n = int(graph.n_vertices)
         self.n = n
@@ -249,15 +252,11 @@ class Graph:
         d = gfd_graph_desc()
         d.n_vertices = n
         d.n_edges = int(dst.shape[0])
-        d.n_attrs = int(np.asarray(graph.attrs).shape[0]) if n else int(np.asarray(graph.attrs).shape[0])
+        d.n_attrs = int(np.asarray(graph.attrs).shape[0])
         d.out_off, d.out_dst, d.out_elabel = _ptr(off), _ptr(dst), _ptr(lab)
         keep = [off, dst, lab, vl, at]
-        if with_reverse:
-            src = np.repeat(np.arange(n, dtype=np.int64), np.diff(off))
-            order = np.lexsort((src, dst))
-            ioff = np.zeros(n + 1, dtype=np.int64)
-            np.cumsum(np.bincount(dst, minlength=n), out=ioff[1:])
-            isrc, ilab = _i32(src[order]), _i32(lab[order])
+        if reverse is not None:
+            ioff, isrc, ilab = _i64(reverse[0]), _i32(reverse[1]), _i32(reverse[2])
             keep += [ioff, isrc, ilab]
             d.in_off, d.in_src, d.in_elabel = _ptr(ioff), _ptr(isrc), _ptr(ilab)
         d.vlabel, d.attrs = _ptr(vl), _ptr(at)
@@ -358,8 +357,8 @@ def node_candidates_noalloc(g: Graph, gfd, node: int, out_ptr: int, out_cap: int
     return int(n.value)
 
 
-def graph_load(graph, stream=None, with_reverse: bool = False) -> Graph:
-    return Graph(graph, stream, with_reverse)
+def graph_load(graph, stream=None, reverse=None) -> Graph:
+    return Graph(graph, stream, reverse)
 
 
 def violations_all(results) -> list:

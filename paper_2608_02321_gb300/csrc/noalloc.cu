@@ -1,12 +1,12 @@
 // gfd_node_candidates_noalloc: the candidate filter of one pattern node
 // (label, degree and self-loop test), computed without allocating any device
-// memory. It exists for callers that are not allowed to allocate: code that
-// runs while a CUDA stream is being captured (an allocation there either fails
-// or breaks the capture), servers whose device memory is owned by another
-// allocator or budgeted up front, and real-time threads that cannot afford the
-// device-wide synchronisation cudaMalloc and cudaFree may cause. The caller
-// passes the graph handle (already resident), the GFD, and a device buffer for
-// the output; the only temporary storage is the file-scope array below.
+// memory. It is meant for callers that may not allocate: a server whose device
+// memory is handed out by its own allocator or reserved up front under a fixed
+// budget (a library cudaMalloc would bypass that accounting, or fail once the
+// reservation holds the free memory), and latency-bound threads that cannot
+// wait for cudaFree, which synchronises the whole device. The caller passes
+// the graph handle (already resident), the GFD, and a device buffer for the
+// output; the only temporary storage is the file-scope array below.
 //
 // The kernel is a single-pass, order-preserving stream compaction: blocks take
 // tiles of TILE consecutive vertices in order from an atomic counter, count the
@@ -41,6 +41,7 @@ static __device__ __align__(256) unsigned long long g_na_scratch[NA_HEADER + NA_
 
 std::mutex g_na_mu;
 void* g_na_ptr[64] = {};  // device address of g_na_scratch, per device
+int g_na_sms[64] = {};    // multiprocessor count, per device
 
 __global__ void __launch_bounds__(NA_THREADS)
 k_node_candidates(DevGraph g, FilterKey key, unsigned long long* scratch, int32_t* out, uint64_t cap,
@@ -121,9 +122,10 @@ k_node_candidates(DevGraph g, FilterKey key, unsigned long long* scratch, int32_
     }
 }
 
-// Device address of the scratch array on the current device (looked up once
-// per device; the host-side symbol is only a stand-in and must not be passed).
-int scratch_ptr(unsigned long long** out) {
+// Device address of the scratch array on the current device and the device's
+// multiprocessor count, looked up once per device (the host-side symbol is only
+// a stand-in for the array and must never be handed to a kernel).
+int scratch_ptr(unsigned long long** out, int* sms) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -133,12 +135,17 @@ int scratch_ptr(unsigned long long** out) {
     }
     std::lock_guard<std::mutex> lock(g_na_mu);
     if (!g_na_ptr[dev]) {
+        int n_sm = 0;
+        e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(multiprocessors)");
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_na_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_na_sms[dev] = n_sm > 0 ? n_sm : 1;
         g_na_ptr[dev] = p;
     }
     *out = (unsigned long long*)g_na_ptr[dev];
+    *sms = g_na_sms[dev];
     return GFD_OK;
 }
 
@@ -165,12 +172,14 @@ int node_candidates_noalloc(const gfd_graph* g, const gfd_gfd* phi, int32_t node
     if (int rc = make_plan(phi, g->n_attrs, g->plan_stats(), &plan)) return rc;
     const FilterKey key = plan.key[plan.level_of[node]];
     unsigned long long* scratch = nullptr;
-    if (int rc = scratch_ptr(&scratch)) return rc;
+    int sms = 1;
+    if (int rc = scratch_ptr(&scratch, &sms)) return rc;
     cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : g->stream;
     cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (NA_HEADER + ntiles), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(scratch)");
     if (ntiles > 0) {
-        const int grid = (int)std::min<uint64_t>(ntiles, 152 * 4);
+        // four resident blocks per multiprocessor take the tiles in order
+        const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)sms * 4);
         k_node_candidates<<<grid, NA_THREADS, 0, st>>>(g->dg, key, scratch, d_out, (uint64_t)out_cap,
                                                        (uint32_t)ntiles);
         e = cudaGetLastError();

@@ -1343,6 +1343,22 @@ int results_sort_copy(gfd_result* const* rs, int n, int32_t* out, uint64_t capac
         return GFD_ERR_INVALID_ARG;
     }
     if (total == 0) return GFD_OK;
+    // Each result's violation list is written on the stream of the call that
+    // made it (the split runs after that call returns). The sort runs on the
+    // first such stream, so it first waits for every other one.
+    std::vector<cudaStream_t> waited;
+    for (int r = 0; r < n; r++) {
+        const cudaStream_t rs_st = rs[r]->stream;
+        if (!rs[r]->n_viol || rs_st == st || std::find(waited.begin(), waited.end(), rs_st) != waited.end())
+            continue;
+        waited.push_back(rs_st);
+        cudaEvent_t ev = nullptr;
+        GFD_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaError_t e = cudaEventRecord(ev, rs_st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+        cudaEventDestroy(ev);
+        if (e != cudaSuccess) return cuda_fail(e, "ordering the violation sort after the result's stream");
+    }
     if (total >= ((uint64_t)1 << 32)) {  // the carried permutation is 32-bit: one result at a time
         for (int r = 0; r < n; r++)
             if (int rc = result_sort_copy(rs[r], out + src[r].int_off)) return rc;

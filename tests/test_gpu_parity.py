@@ -15,7 +15,7 @@ from synth.graphs import graph_from_edges, random_small_graph
 
 from cases import (complete_bidirected, directed_cycle, edges_graph, golden_cases, out_star,
                    random_case, star_q, undirected_q)
-from gpu_util import assert_same, gpu_graph, gpu_run
+from gpu_util import assert_same, gpu_graph, gpu_run, reverse_csr
 
 pytestmark = pytest.mark.gpu
 
@@ -175,7 +175,7 @@ def test_violation_capacity_regrows(lib, oracle_mod):
 
 def test_reverse_csr_given(lib, oracle_mod):
     g, q = random_case(3, n_vertices=7)
-    assert_same(gpu_run(gpu_graph(g, with_reverse=True), q), oracle_mod.validate(g, q), "reverse given")
+    assert_same(gpu_run(gpu_graph(g, reverse=reverse_csr(g)), q), oracle_mod.validate(g, q), "reverse given")
 
 
 def test_rejects_invalid_inputs(lib):

@@ -1,12 +1,14 @@
 """The allocation-free entry point (gfd_node_candidates_noalloc) against the
-existing one (gfd_validate). For callers that cannot allocate device memory
-(inside a stream capture, under a foreign allocator or a fixed budget), the
-library offers the candidate filter of one pattern node with all scratch in a
-fixed array of its own. A single-node GFD with X empty and Y = false has
-exactly those candidates as its violations, so gfd_validate gives the expected
-list; for larger patterns the per-node counts add up to the candidate total
-that gfd_validate reports without refinement. Each check runs twice in a row,
-because every call reuses the same scratch array."""
+existing one (gfd_validate). Some callers may not allocate device memory: a
+server whose device memory comes from its own allocator or a budget reserved up
+front, or a latency-bound thread that cannot wait for cudaFree's device-wide
+synchronisation. For them the library offers the candidate filter of one
+pattern node with all scratch in a fixed array of its own. A single-node GFD
+with X empty and Y = false has exactly those candidates as its violations, so
+gfd_validate gives the expected list; for larger patterns the per-node counts
+add up to the candidate total that gfd_validate reports without refinement.
+Each check runs twice in a row, because every call reuses the same scratch
+array."""
 import numpy as np
 import pytest
 
