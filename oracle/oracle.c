@@ -212,16 +212,30 @@ static int og_lit_holds(const og_state *s, const og_lit *l) {
     return va == vb;
 }
 
+/* Does the match in s->h satisfy X (every X literal holds)? */
+static int og_x_holds(const og_state *s) {
+    const og_gfd *q = s->q;
+    int i, x_ok = 1;
+    for (i = 0; i < q->nx; i++) x_ok = x_ok && og_lit_holds(s, &q->X[i]);
+    return x_ok;
+}
+
+/* Is the match in s->h a violation: h satisfies X, and Y is false or some Y
+ * literal fails? */
+static int og_is_violation(const og_state *s) {
+    const og_gfd *q = s->q;
+    int i, y_ok = 1;
+    if (!og_x_holds(s)) return 0;
+    if (q->y_false) return 1;
+    for (i = 0; i < q->ny; i++) y_ok = y_ok && og_lit_holds(s, &q->Y[i]);
+    return !y_ok;
+}
+
 static void og_record(og_state *s) {
     const og_gfd *q = s->q;
-    int i, x_ok = 1, y_ok = 1;
     s->n_matches++;
-    for (i = 0; i < q->nx; i++) x_ok = x_ok && og_lit_holds(s, &q->X[i]);
-    s->n_x_matches += (uint64_t)x_ok;
-    if (!x_ok) return;
-    if (q->y_false) y_ok = 0;
-    else for (i = 0; i < q->ny; i++) y_ok = y_ok && og_lit_holds(s, &q->Y[i]);
-    if (y_ok) return;
+    s->n_x_matches += (uint64_t)og_x_holds(s);
+    if (!og_is_violation(s)) return;
     if (s->n_viol == s->cap_viol) {
         s->cap_viol = s->cap_viol ? 2 * s->cap_viol : 1024;
         s->viol = (int32_t *)realloc(s->viol, sizeof(int32_t) * (size_t)s->cap_viol * (size_t)q->k);
@@ -368,6 +382,34 @@ int og_validate_budget(const og_graph *g, const og_gfd *q, const int32_t *roots,
 int og_validate(const og_graph *g, const og_gfd *q, const int32_t *roots, int64_t n_roots,
                 uint64_t *n_matches, int32_t **viol_out, int64_t *n_viol) {
     return og_validate_mode(g, q, 1, roots, n_roots, 0.0, n_matches, viol_out, n_viol, NULL, NULL);
+}
+
+/* The literal check alone on given matches: flags[i] = 1 when the k-tuple
+ * tuples[i] = (h(x_0), ..., h(x_{k-1})), taken as a match of q's pattern (not
+ * checked as one), is a violation of q, else 0. Returns 0, or 1 for a
+ * malformed GFD or an out-of-range vertex. */
+int og_violating(const og_graph *g, const og_gfd *q, const int32_t *tuples, int64_t n, uint8_t *flags) {
+    og_state s;
+    int64_t t;
+    int i;
+    memset(&s, 0, sizeof(s));
+    s.g = g; s.q = q;
+    if (q->k < 1 || q->k > OG_MAXK) return 1;
+    for (i = 0; i < q->nx + q->ny; i++) {
+        const og_lit *l = i < q->nx ? &q->X[i] : &q->Y[i - q->nx];
+        if (l->x < 0 || l->x >= q->k || l->a < 0 || l->a >= g->n_attrs) return 1;
+        if (l->kind == 1 && (l->y < 0 || l->y >= q->k || l->b < 0 || l->b >= g->n_attrs))
+            return 1;
+        if (l->kind != 0 && l->kind != 1) return 1;
+    }
+    for (t = 0; t < n; t++) {
+        for (i = 0; i < q->k; i++) {
+            s.h[i] = tuples[t * q->k + i];
+            if (s.h[i] < 0 || s.h[i] >= g->n) return 1;
+        }
+        flags[t] = (uint8_t)og_is_violation(&s);
+    }
+    return 0;
 }
 
 /* --------------------------------------------------------------- sorting */

@@ -68,6 +68,8 @@ def bind_library(path: str):
     lib.og_validate_mode.argtypes = [C.c_void_p, C.POINTER(_Gfd), C.c_int, C.c_void_p, C.c_int64, C.c_double,
                                      C.POINTER(C.c_uint64), C.POINTER(C.c_void_p),
                                      C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_uint64)]
+    lib.og_violating.restype = C.c_int
+    lib.og_violating.argtypes = [C.c_void_p, C.POINTER(_Gfd), C.c_void_p, C.c_int64, C.c_void_p]
     lib.og_free.argtypes = [C.c_void_p]
     return lib
 
@@ -228,6 +230,21 @@ def validate_within(og: OracleGraph, gfd, roots, seconds: float, induced: bool =
         lib.og_free(vp)
     del keep
     return int(nm.value), sort_tuples(out), int(done.value)
+
+
+def violating(og: OracleGraph, gfd, matches: np.ndarray) -> np.ndarray:
+    """The rows of `matches` ([n, k] tuples taken as matches of gfd's pattern)
+    that are violations of gfd (X holds, and Y is false or fails): the
+    literal check of Section II on its own, in the input order."""
+    lib = og._lib
+    s, keep = _gfd_struct(gfd)
+    t = np.ascontiguousarray(matches, dtype=np.int32).reshape(-1, gfd.k)
+    flags = np.zeros(t.shape[0], dtype=np.uint8)
+    rc = lib.og_violating(og._h, C.byref(s), _ptr(t), int(t.shape[0]), _ptr(flags))
+    del keep
+    if rc != 0:
+        raise ValueError("oracle rejected the GFD or a tuple")
+    return t[flags.astype(bool)]
 
 
 def sort_tuples(t: np.ndarray) -> np.ndarray:

@@ -29,7 +29,7 @@ MUTANTS = {
     "no_self_loop_check": ("if (!og_pair_ok(s->qedge[u][u], og_edge(g, v, v))) return 0;", ""),
     "absent_is_a_value": [("if (va == OG_ABSENT) return 0;", ""),
                           ("if (vb == OG_ABSENT) return 0;", "")],
-    "ignores_false": ("if (q->y_false) y_ok = 0;", ""),
+    "ignores_false": ("if (q->y_false) return 1;", ""),
     "ignores_edge_labels": ("return og_label_ok(ql, gl);", "return 1;"),
     "transposed_edge": ("og_pair_ok(s->qedge[u][w], og_edge(g, v, hw))",
                         "og_pair_ok(s->qedge[u][w], og_edge(g, hw, v))"),
@@ -43,7 +43,10 @@ MUTANTS = {
     "non_induced_mode_drops_required_edges": ("if (!og_induced && ql == OG_NOEDGE) return 1;",
                                               "if (!og_induced) return 1;"),
     # count of X-satisfying matches
-    "x_count_ignores_x": ("s->n_x_matches += (uint64_t)x_ok;", "s->n_x_matches += 1;"),
+    "x_count_ignores_x": ("s->n_x_matches += (uint64_t)og_x_holds(s);", "s->n_x_matches += 1;"),
+    # the literal check on given matches
+    "violating_row_stride": ("s.h[i] = tuples[t * q->k + i];", "s.h[i] = tuples[t + i];"),
+    "violating_ignores_y": ("flags[t] = (uint8_t)og_is_violation(&s);", "flags[t] = (uint8_t)og_x_holds(&s);"),
     # disconnected patterns
     "component_start_skips_last_vertex": ("if (s->pnode[i] < 0) { a = 0; b = g->n; hp = -1; }",
                                           "if (s->pnode[i] < 0) { a = 0; b = g->n - 1; hp = -1; }"),
@@ -98,6 +101,17 @@ def _pins_pass(lib) -> bool:
         nx, v = O.validate(g, q, lib=lib, count="x")
         bnx, bv = brute_force(g, q, count="x")
         if nx != bnx or not np.array_equal(v, bv):
+            return False
+    # the literal check on given matches: the twin X = {} -> false lists every
+    # match; its violating rows are the GFD's violations
+    og_lib = lib
+    for seed in range(40):
+        g, q = random_case(seed)
+        twin = GFD(q.node_label, q.edges, [], [], True)
+        _, matches = O.validate(g, twin, lib=og_lib)
+        _, v = O.validate(g, q, lib=og_lib)
+        got = O.sort_tuples(O.violating(O.OracleGraph(g, og_lib), q, matches))
+        if not np.array_equal(got, v):
             return False
     return True
 

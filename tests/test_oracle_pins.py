@@ -228,3 +228,18 @@ def test_validate_within_is_a_root_prefix(oracle_mod):
         want = oracle_mod.validate(og, q, roots=roots[:done2]) if done2 else (0, np.zeros((0, q.k), np.int32))
         assert nm2 == want[0]
         np.testing.assert_array_equal(v2, want[1])
+
+
+# ------------------------------------------------ literal check on given matches
+@pytest.mark.parametrize("seed", range(40))
+def test_violating_on_match_list_equals_brute_force(oracle_mod, seed):
+    """The twin X = {} -> false of a GFD has every match as a violation
+    (Section II: nothing satisfies false); the literal check applied to that
+    list must give exactly the brute-force violations of the GFD itself."""
+    g, q = random_case(seed)
+    twin = GFD(q.node_label, q.edges, [], [], True)
+    nm, matches = oracle_mod.validate(g, twin)
+    bnm, bv = brute_force(g, q)
+    assert nm == bnm == matches.shape[0]
+    got = oracle_mod.sort_tuples(oracle_mod.violating(oracle_mod.OracleGraph(g), q, matches))
+    np.testing.assert_array_equal(got, bv)
