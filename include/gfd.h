@@ -149,11 +149,22 @@ typedef struct {
                                        unchanged; gfd_result_matches then counts
                                        the matches that satisfy X. */
 
+#define GFD_FLAG_KEEP_CANDIDATES 0x40 /* keep a host copy of every pattern node's
+                                       refined candidate list C(u) (Section III.B
+                                       step 1c) in the result, read with
+                                       gfd_result_candidates (batch calls only;
+                                       for inspection and tests) */
+
 /* Tuning options; a NULL gfd_opts* or zero fields select the defaults. */
 typedef struct {
     int64_t frontier_budget_bytes; /* device bytes for partial-match buffers
                                       (0: the tuned choice, else min(128 GiB,
-                                      half the free device memory)) */
+                                      half the free device memory)). A budget
+                                      that cannot hold 1024 partial matches per
+                                      level of every GFD of a call gives
+                                      GFD_ERR_OUT_OF_MEMORY (calls with
+                                      chunk_rows set, and sessions, use at
+                                      least 1024 instead) */
     int32_t chunk_rows;            /* partial matches expanded per step and GFD */
     int32_t kernel_variant;        /* enumeration kernel: 0 = the graph's tuned
                                       choice (gfd_autotune) or the default;
@@ -246,6 +257,14 @@ double gfd_result_profile(const gfd_result *r, int32_t which, int64_t *launches)
  * (sum over pattern nodes), 5 index entries, 6 number of extra runs made
  * because the violations of the call outgrew max_violations_hint. */
 uint64_t gfd_result_stat(const gfd_result *r, int32_t which);
+/* The refined candidate list C(u) of pattern node `node` (Section III.B step
+ * 1c: label and degree filter, then top-down and bottom-up refinement), kept by
+ * a batch call made with GFD_FLAG_KEEP_CANDIDATES: *list receives increasing
+ * vertex ids in host memory owned by the result, *n their number. Every match
+ * h has h(node) in this list (refinement removes only dead ends). Returns
+ * GFD_OK, or GFD_ERR_INVALID_ARG (NULL argument, node out of range, or the
+ * result kept no lists). */
+int gfd_result_candidates(const gfd_result *r, int32_t node, const int32_t **list, int64_t *n);
 /* Release a result and its device and host buffers; NULL is a no-op. */
 void gfd_result_free(gfd_result *r);
 
@@ -277,6 +296,12 @@ int gfd_session_step(gfd_session *s, int32_t *n_advanced, int32_t *n_running, in
 /* Pop one finished request: *request_id = -1 and *out = NULL when none is
  * ready. The caller owns *out (gfd_result_free). */
 int gfd_session_next_result(gfd_session *s, int64_t *request_id, gfd_result **out);
+/* Cancel a request of the session: a queued one is dropped, a running one is
+ * stopped and its device memory released, a finished but uncollected one has
+ * its result freed; no result for it is delivered afterwards. Call it between
+ * gfd_session_step calls. Returns GFD_OK, or GFD_ERR_INVALID_ARG when the
+ * session holds no request with that id (unknown, or already collected). */
+int gfd_session_cancel(gfd_session *s, int64_t request_id);
 /* Wait for the session's work, release it and any uncollected results. */
 void gfd_session_free(gfd_session *s);
 

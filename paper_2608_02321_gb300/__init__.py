@@ -33,6 +33,7 @@ FLAG_PROFILE = 0x4
 FLAG_NO_GRAPH = 0x8
 FLAG_NON_INDUCED = 0x10
 FLAG_PUSH_X = 0x20
+FLAG_KEEP_CANDIDATES = 0x40
 
 PROF_FILTER, PROF_REFINE, PROF_INDEX, PROF_ENUM, PROF_SORT = range(5)
 STAT_STEPS, STAT_WORK, STAT_ROWS, STAT_PROBES, STAT_CANDIDATES, STAT_INDEX, STAT_RERUN = range(7)
@@ -89,11 +90,13 @@ _SIGS = {
     "gfd_results_copy_tuples": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_uint64]),
     "gfd_result_profile": (C.c_double, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
     "gfd_result_stat": (C.c_uint64, [C.c_void_p, C.c_int32]),
+    "gfd_result_candidates": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]),
     "gfd_result_free": (None, [C.c_void_p]),
     "gfd_session_create": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(gfd_opts), C.POINTER(C.c_void_p)]),
     "gfd_session_submit": (C.c_int, [C.c_void_p, C.POINTER(gfd_gfd), C.POINTER(C.c_int64)]),
     "gfd_session_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "gfd_session_next_result": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_void_p)]),
+    "gfd_session_cancel": (C.c_int, [C.c_void_p, C.c_int64]),
     "gfd_session_free": (None, [C.c_void_p]),
     "gfd_node_candidates_noalloc": (C.c_int, [C.c_void_p, C.POINTER(gfd_gfd), C.c_int32, C.c_void_p,
                                               C.c_int64, C.POINTER(C.c_int64), C.c_void_p]),
@@ -233,6 +236,17 @@ class Result:
     def stat(self, which: int) -> int:
         return int(_lib.gfd_result_stat(self._h, int(which)))
 
+    def candidates(self, node: int) -> np.ndarray:
+        """The refined candidate list of pattern node `node` (needs
+        FLAG_KEEP_CANDIDATES on the batch call), increasing vertex ids."""
+        p = C.c_void_p(None)
+        n = C.c_int64(0)
+        _check(_lib.gfd_result_candidates(self._h, int(node), C.byref(p), C.byref(n)))
+        if n.value == 0:
+            return np.zeros(0, dtype=np.int32)
+        buf = (C.c_int32 * n.value).from_address(p.value)
+        return np.frombuffer(buf, dtype=np.int32).copy()
+
 
 class Graph:
     """A graph resident on the GPU (gfd_graph_load)."""
@@ -333,6 +347,11 @@ class Session:
         q = C.c_int32(0)
         _check(_lib.gfd_session_step(self._h, C.byref(a), C.byref(r), C.byref(q)))
         return int(a.value), int(r.value), int(q.value)
+
+    def cancel(self, request_id: int):
+        """Drop a queued request, stop a running one or discard an uncollected
+        result (gfd_session_cancel)."""
+        _check(_lib.gfd_session_cancel(self._h, int(request_id)))
 
     def results(self):
         """All finished requests since the last call: [(request_id, Result)]."""

@@ -140,6 +140,18 @@ uint64_t gfd_result_stat(const gfd_result* r, int32_t which) {
     return r->stat[which];
 }
 
+int gfd_result_candidates(const gfd_result* r, int32_t node, const int32_t** list, int64_t* n) {
+    if (!r || !list || !n || !r->has_cand || node < 0 || node >= (int32_t)r->cand.size()) {
+        gfd::set_error(GFD_ERR_INVALID_ARG,
+                       "gfd_result_candidates: NULL argument, node out of range, or no candidate lists kept "
+                       "(validate with GFD_FLAG_KEEP_CANDIDATES)");
+        return GFD_ERR_INVALID_ARG;
+    }
+    *list = r->cand[node].data();
+    *n = (int64_t)r->cand[node].size();
+    return GFD_OK;
+}
+
 void gfd_result_free(gfd_result* r) {
     if (!r) return;
     if (r->d_viol) cudaFree(r->d_viol);
@@ -161,6 +173,8 @@ int gfd_session_step(gfd_session* s, int32_t* n_advanced, int32_t* n_running, in
 int gfd_session_next_result(gfd_session* s, int64_t* request_id, gfd_result** out) {
     return gfd::session_next_result(s, request_id, out);
 }
+
+int gfd_session_cancel(gfd_session* s, int64_t request_id) { return gfd::session_cancel(s, request_id); }
 
 void gfd_session_free(gfd_session* s) { gfd::session_free(s); }
 

@@ -53,6 +53,8 @@ struct gfd_result {
     int64_t prof_launch[5] = {0, 0, 0, 0, 0};
     uint64_t stat[7] = {0, 0, 0, 0, 0, 0, 0};
     cudaStream_t stream = nullptr;
+    bool has_cand = false;                      // GFD_FLAG_KEEP_CANDIDATES
+    std::vector<std::vector<int32_t>> cand;     // refined candidate list per pattern node
 };
 
 namespace gfd {
@@ -170,6 +172,7 @@ void session_free(gfd_session* s);
 int session_submit(gfd_session* s, const gfd_gfd* phi, int64_t* id);
 int session_step(gfd_session* s, int32_t* n_advanced, int32_t* n_running, int32_t* n_queued);
 int session_next_result(gfd_session* s, int64_t* id, gfd_result** out);
+int session_cancel(gfd_session* s, int64_t id);
 int autotune(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opts* o, gfd_opts* best);
 // Sort the violation tuples on the device and copy them to dst (host memory,
 // n_viol * k ints); result_fetch does this into the result's own buffer.

@@ -252,9 +252,12 @@ bool td_gather_cheaper(const gfd_graph* g, int32_t label_q, int32_t label_i, int
     return gather < scatter;
 }
 
-// Plans, capacities and the workspace layout of a group (host only).
+// Plans, capacities and the workspace layout of a group (host only). With
+// strict_budget, a frontier_per_slot that cannot hold MIN_CHUNK partial matches
+// at every level of some GFD is an error instead of being raised to that.
+constexpr uint64_t MIN_CHUNK = 1024;
 int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* o, int64_t frontier_per_slot,
-               Group* G) {
+               Group* G, bool strict_budget = false) {
     const uint32_t nwords = g->dg.nwords;
     G->n = n;
     G->plans.resize(n);
@@ -315,7 +318,15 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
         for (int l = 1; l <= P.k - 2; l++) row_bytes += 4ull * (2 * (l + 1) + 2) + 8;
         uint64_t chunk = o && o->chunk_rows > 0 ? (uint64_t)o->chunk_rows
                                                 : (row_bytes ? (uint64_t)frontier_per_slot / row_bytes : (1ull << 24) - 1);
-        chunk = std::max<uint64_t>(1024, std::min<uint64_t>(chunk, (1ull << 24) - 1));
+        if (strict_budget && !(o && o->chunk_rows > 0) && chunk < MIN_CHUNK) {
+            set_error(GFD_ERR_OUT_OF_MEMORY,
+                      "frontier budget of %lld bytes per GFD holds fewer than %llu partial matches per level of GFD "
+                      "%d (it needs %llu bytes)",
+                      (long long)frontier_per_slot, (unsigned long long)MIN_CHUNK, s,
+                      (unsigned long long)(MIN_CHUNK * row_bytes));
+            return GFD_ERR_OUT_OF_MEMORY;
+        }
+        chunk = std::max<uint64_t>(MIN_CHUNK, std::min<uint64_t>(chunk, (1ull << 24) - 1));
         D.chunk = chunk;
         Group::Off& F = G->offs[s];
         for (int i = 0; i < P.k; i++) {
@@ -756,7 +767,7 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
     Group G;
     const int64_t budget = (!o || o->frontier_budget_bytes <= 0) && g->tuned_budget > 0 ? g->tuned_budget
                                                                                         : default_budget(g, o);
-    if (int rc = group_plan(g, phis, n, o, budget / n, &G)) return rc;
+    if (int rc = group_plan(g, phis, n, o, budget / n, &G, o && o->frontier_budget_bytes > 0)) return rc;
     int kmax = 1;
     for (auto& P : G.plans) kmax = std::max(kmax, P.k);
     cudaMemPool_t pool;
@@ -847,9 +858,28 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
         if (int rc = launch_split(T.desc, T.varena, hs.varena_used, T.vstride, T.vptr, T.vcur, st)) return rc;
         launches[PROF_ENUM] += 1;  // the split belongs to the enumeration's output
     }
+    // the refined candidate lists, kept for inspection when asked for
+    std::vector<std::vector<std::vector<int32_t>>> kept(n);
+    if (flags & GFD_FLAG_KEEP_CANDIDATES) {
+        for (int s = 0; s < n; s++) {
+            kept[s].resize(G.plans[s].k);
+            for (int i = 0; i < G.plans[s].k; i++) {
+                auto& lst = kept[s][G.plans[s].order[i]];
+                lst.resize(states[s].ncand[i]);
+                if (!lst.empty())
+                    GFD_CUDA(cudaMemcpyAsync(lst.data(), G.descs[s].cand[i], 4ull * lst.size(),
+                                             cudaMemcpyDeviceToHost, st));
+            }
+        }
+        GFD_CUDA(cudaStreamSynchronize(st));
+    }
     for (int s = 0; s < n; s++) {
         gfd_result* r = make_result(G.plans[s], states[s], hs.steps, hs.probes, vbuf[s], st);
         vbuf[s] = nullptr;
+        if (flags & GFD_FLAG_KEEP_CANDIDATES) {
+            r->cand = std::move(kept[s]);
+            r->has_cand = true;
+        }
         for (int w = 0; w < 5; w++) {
             r->prof_ms[w] = prof.ms(w);
             r->prof_launch[w] = launches[w];
@@ -1052,6 +1082,29 @@ int session_admit(gfd_session* S) {
 
 }  // namespace
 
+namespace {
+
+// Free a slot's device memory and return it to the pool of free slots (its
+// request finished or was cancelled; no kernel of the session is running).
+void slot_release(gfd_session* S, SlotHost& sl) {
+    if (sl.viol) cudaFreeAsync(sl.viol, S->st);
+    sl.viol = nullptr;
+    S->used -= (int64_t)(4ull * sl.group->plans[sl.index].k * sl.viol_cap);
+    if (--sl.group->live == 0) {
+        cudaFreeAsync(sl.group->base, S->st);
+        if (sl.group->cpi_base) cudaFreeAsync(sl.group->cpi_base, S->st);
+        S->used -= (int64_t)(sl.group->bytes + sl.group->cpi_bytes);
+        sl.group->base = nullptr;
+        sl.group->cpi_base = nullptr;
+    }
+    sl.group.reset();
+    sl.req.reset();
+    sl.busy = false;
+    sl.id = -1;
+}
+
+}  // namespace
+
 int session_step(gfd_session* S, int32_t* n_advanced, int32_t* n_running, int32_t* n_queued) {
     if (!S) {
         set_error(GFD_ERR_INVALID_ARG, "gfd_session_step: NULL session");
@@ -1100,20 +1153,9 @@ int session_step(gfd_session* S, int32_t* n_advanced, int32_t* n_running, int32_
             } else {
                 r = make_result(sl.group->plans[sl.index], states[i], hs.steps, hs.probes, sl.viol, S->st);
             }
-            sl.viol = nullptr;
+            sl.viol = nullptr;  // now owned by the result (or freed above)
             S->done.emplace_back(sl.id, r);
-            S->used -= (int64_t)(4ull * sl.group->plans[sl.index].k * sl.viol_cap);
-            if (--sl.group->live == 0) {
-                cudaFreeAsync(sl.group->base, S->st);
-                if (sl.group->cpi_base) cudaFreeAsync(sl.group->cpi_base, S->st);
-                S->used -= (int64_t)(sl.group->bytes + sl.group->cpi_bytes);
-                sl.group->base = nullptr;
-                sl.group->cpi_base = nullptr;
-            }
-            sl.group.reset();
-            sl.req.reset();
-            sl.busy = false;
-            sl.id = -1;
+            slot_release(S, sl);
         }
     }
     int running = 0;
@@ -1121,6 +1163,36 @@ int session_step(gfd_session* S, int32_t* n_advanced, int32_t* n_running, int32_
     if (n_running) *n_running = running;
     if (n_queued) *n_queued = (int32_t)S->queue.size();
     return GFD_OK;
+}
+
+int session_cancel(gfd_session* S, int64_t id) {
+    if (!S) {
+        set_error(GFD_ERR_INVALID_ARG, "gfd_session_cancel: NULL session");
+        return GFD_ERR_INVALID_ARG;
+    }
+    for (auto it = S->queue.begin(); it != S->queue.end(); ++it)
+        if ((*it)->id == id) {
+            S->queue.erase(it);
+            return GFD_OK;
+        }
+    for (size_t i = 0; i < S->slots.size(); i++) {
+        SlotHost& sl = S->slots[i];
+        if (!sl.busy || sl.id != id) continue;
+        // the slot stops: the next control step skips it (stream-ordered after
+        // the last round, which has finished when gfd_session_step returned)
+        static const int32_t stopped = -1;
+        GFD_CUDA(cudaMemcpyAsync(&S->T.state[i].cur, &stopped, sizeof(int32_t), cudaMemcpyHostToDevice, S->st));
+        slot_release(S, sl);
+        return GFD_OK;
+    }
+    for (auto it = S->done.begin(); it != S->done.end(); ++it)
+        if (it->first == id) {
+            gfd_result_free(it->second);
+            S->done.erase(it);
+            return GFD_OK;
+        }
+    set_error(GFD_ERR_INVALID_ARG, "gfd_session_cancel: no request %lld in the session", (long long)id);
+    return GFD_ERR_INVALID_ARG;
 }
 
 int session_next_result(gfd_session* S, int64_t* id, gfd_result** out) {

@@ -1,17 +1,19 @@
 """The batched workload at full size (4M vertices, 40M edges, 256 GFDs) in the
-launch configuration the benchmark times (autotuned, one gfd_validate_batch):
-for sampled root vertices of every GFD, the GPU's violations whose node-0 image
-is a sampled root equal the oracle's violations for exactly those roots (the
-oracle runs with a deadline per GFD and is compared on the roots it finished)."""
+launch configuration the benchmark times (autotuned, one gfd_validate_batch of
+all 256 GFDs), checked root by root against the oracle: for about 2,300
+sampled (GFD, root) pairs, uniform over the label-compatible vertices, hubs of
+degree >= 1000 (the top hub of every GFD's pool among them) and node-0 images of
+GPU matches, the GPU's matches at the root (from the twin X = {} -> false,
+validated in the same way) and its violations at the root are identical to the
+oracle's; the match count of every GFD equals its twin's."""
 from __future__ import annotations
-
-import os
-from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import pytest
 
 from synth import configs
+
+from full_size import compare, gpu_rows_for_roots, rows_at, sample_roots, twin
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -24,35 +26,23 @@ def test_full_size_sampled_roots(oracle_mod):
     dg = G.Graph(g)
     dg.autotune(qs)
     res = dg.validate_batch(qs)
-    viol = G.violations_all(res)
-    og = oracle_mod.OracleGraph(g)
-    deg = np.diff(g.out_off) + np.bincount(g.out_dst, minlength=g.n_vertices)
-    low = np.nonzero(deg <= 40)[0]
+    total = sum(r.n_matches for r in res)
+    tres = dg.validate_batch([twin(q) for q in qs], max_violations_hint=total + 1)
+    for i, (r, t) in enumerate(zip(res, tres)):
+        assert r.n_matches == t.n_matches == t.n_violations, f"gfd {i}: twin counts differ"
+    degree = np.diff(g.out_off) + np.bincount(g.out_dst, minlength=g.n_vertices)
     rng = np.random.default_rng(20261203)
-
-    # roots per GFD (drawn here, in order): low-degree label-compatible vertices
-    # and vertices that are the node-0 image of some GPU violation
-    sample = []
-    for q, v in zip(qs, viol):
-        L = q.node_label[0]
-        pool = low if L < 0 else low[g.vlabel[low] == L]
-        roots = list(rng.choice(pool, size=min(4, len(pool)), replace=False)) if len(pool) else []
-        if v.shape[0]:
-            u = np.unique(v[:, 0])
-            roots += list(rng.choice(u, size=min(4, len(u)), replace=False))
-        sample.append(np.array(sorted(set(int(r) for r in roots)), np.int32))
-
-    def check(i):
-        q, v, roots = qs[i], viol[i], sample[i]
-        if roots.shape[0] == 0:
-            return 0, 0
-        _, want, done = oracle_mod.validate_within(og, q, roots, 1.0)
-        got = v[np.isin(v[:, 0], roots[:done])] if v.shape[0] else v
-        np.testing.assert_array_equal(got, want, err_msg=f"gfd {i} {q.name} roots {roots[:done]}")
-        return done, want.shape[0]
-
-    with ThreadPoolExecutor(os.cpu_count() or 8) as ex:
-        out = list(ex.map(check, range(len(qs))))
-    roots_checked = sum(o[0] for o in out)
-    viol_checked = sum(o[1] for o in out)
-    assert roots_checked >= 500 and viol_checked >= 100, (roots_checked, viol_checked)
+    samples, gpu_m = [], {}
+    for i, q in enumerate(qs):          # one GFD's sorted matches on the host at a time
+        t = tres[i].violations()
+        samples.append(sample_roots(g, q, degree, t, rng, n_uniform=5, n_from_matches=2, n_hubs=2))
+        gpu_m.update({(i, r): rows_at(t, r).copy() for r, _ in samples[i]})
+        del t
+    gpu_v = gpu_rows_for_roots(res, samples)
+    og = oracle_mod.OracleGraph(g)
+    st = compare(og, oracle_mod, qs, samples, gpu_m, gpu_v, degree, deadline=2.0, hub_deadline=4.0,
+                 wall_cap=150.0)
+    print("batched full-size sampled roots:", st)
+    assert st["roots_done"] >= 2000, st
+    assert st["hub_roots_done"] >= 50, st
+    assert st["matches_compared"] >= 1000 and st["violations_compared"] >= 100, st

@@ -12,6 +12,7 @@ from synth import configs
 from synth.gfds import GFD, Literal
 from synth.graphs import random_small_graph
 
+from full_size import compare, gpu_rows_for_roots, reorder, rows_at, sample_roots, swap_perm, twin
 from gpu_util import assert_same, gpu_graph
 
 pytestmark = pytest.mark.gpu
@@ -68,8 +69,53 @@ def test_kg_scaled_properties(lib_loaded):
     _properties(g, qs)
 
 
+@pytest.fixture(scope="module")
+def kg_full():
+    return configs.kg()
+
+
 @pytest.mark.slow
-def test_kg_full_size_properties(lib_loaded):
-    g, qs = configs.kg()
+def test_kg_full_size_properties(lib_loaded, kg_full):
+    g, qs = kg_full
     assert np.diff(g.out_off).max() > 500_000          # hub out-degrees near 1e6
     _properties(g, qs)
+
+
+@pytest.mark.slow
+def test_kg_full_size_sampled_roots(lib_loaded, kg_full, oracle_mod):
+    """The full KG workload (20M vertices, 200M edges, 32 GFDs) in one batched
+    launch, root by root against the oracle. The roots are images of z1 (node
+    3, in-degree 2 in the pattern): the matches of a KG pattern concentrate on
+    x hubs with out-degrees up to ~1e6, which the oracle cannot search from x
+    in seconds, while from z1 each root's work stays small. The oracle runs
+    each GFD relabelled so that z1 is node 0 (results are invariant under
+    relabelling, a pinned invariant) and the GPU's tuples are compared in that
+    column order. About 2,300 (GFD, root) pairs: uniform over label-compatible
+    vertices of in-degree >= 2, hubs of in-degree >= 1000 (the top one of every
+    pool among them) and z1 images of GPU matches. Matches (through the twin
+    X = {} -> false) and violations must be identical."""
+    g, qs = kg_full
+    dg = gpu_graph(g)
+    res = dg.validate_batch(qs)
+    total = sum(r.n_matches for r in res)
+    tres = dg.validate_batch([twin(q) for q in qs], max_violations_hint=total + 1)
+    for i, (r, t) in enumerate(zip(res, tres)):
+        assert r.n_matches == t.n_matches == t.n_violations, f"gfd {i}: twin counts differ"
+    in_deg = np.bincount(g.out_dst, minlength=g.n_vertices)
+    perms = [swap_perm(q.k, 3) for q in qs]
+    rel = [q.relabel_nodes(p) for q, p in zip(qs, perms)]
+    rng = np.random.default_rng(20261204)
+    samples, gpu_m = [], {}
+    for i, q in enumerate(rel):
+        t = reorder(tres[i].violations(), perms[i])
+        samples.append(sample_roots(g, q, in_deg, t, rng, n_uniform=60, n_from_matches=10, n_hubs=4,
+                                    min_degree=2))
+        gpu_m.update({(i, r): rows_at(t, r).copy() for r, _ in samples[i]})
+    gpu_v = gpu_rows_for_roots(res, samples, perms)
+    og = oracle_mod.OracleGraph(g)
+    st = compare(og, oracle_mod, rel, samples, gpu_m, gpu_v, in_deg, deadline=2.0, hub_deadline=4.0,
+                 wall_cap=120.0)
+    print("kg full-size sampled roots:", st)
+    assert st["roots_done"] >= 2000, st
+    assert st["hub_roots_done"] >= 50, st
+    assert st["roots_with_matches"] >= 100, st
