@@ -132,31 +132,44 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample(g, qs, seconds: float, threads: int, seed: int = 7):
-    """The oracle over seeded random root samples of every GFD for about
-    `seconds` of wall time on `threads` host threads; the root in progress at
-    the deadline is dropped. Returns (matches, wall seconds, roots searched)."""
+ROOT_SAMPLE_SEED = 20261205
+ROOTS_PER_GFD = 384
+ROOTS_PER_TASK = 64
+TASK_DEADLINE_S = 2.0
+
+
+def fixed_root_tasks(g, qs, per_gfd: int = ROOTS_PER_GFD, seed: int = ROOT_SAMPLE_SEED):
+    """The seeded root sample both CPU legs time: per GFD, `per_gfd` vertices
+    drawn uniformly (images of pattern node 0), in tasks of ROOTS_PER_TASK."""
+    rng = np.random.default_rng(seed)
+    tasks = []
+    for i in range(len(qs)):
+        roots = rng.integers(0, g.n_vertices, size=per_gfd).astype(np.int32)
+        tasks += [(i, roots[a:a + ROOTS_PER_TASK]) for a in range(0, per_gfd, ROOTS_PER_TASK)]
+    return tasks
+
+
+def oracle_sample(g, qs, threads: int, og=None, tasks=None):
+    """The oracle, as it stands, over the fixed root sample on `threads` host
+    threads; each task (ROOTS_PER_TASK roots of one GFD) has TASK_DEADLINE_S, and
+    the roots after the one in progress at its deadline are dropped with their
+    matches (the time is still counted). Returns (matches, wall seconds, roots
+    searched to the end, roots dropped)."""
     from concurrent.futures import ThreadPoolExecutor
     from oracle import oracle
-    og = oracle.OracleGraph(g)
-    rng = np.random.default_rng(seed)
-    per = 16
-    tasks = [(i, rng.integers(0, g.n_vertices, size=per).astype(np.int32))
-             for _ in range(max(1, 100000 // max(1, len(qs) * per))) for i in range(len(qs))]
-    t0 = time.perf_counter()
-    deadline = t0 + seconds
+    og = og or oracle.OracleGraph(g)
+    tasks = tasks if tasks is not None else fixed_root_tasks(g, qs)
 
     def run(task):
-        left = deadline - time.perf_counter()
-        if left <= 0:
-            return 0, 0
         i, rs = task
-        return oracle.count_within(og, qs[i], rs, left)
+        return oracle.count_within(og, qs[i], rs, TASK_DEADLINE_S)
 
+    t0 = time.perf_counter()
     with ThreadPoolExecutor(threads) as ex:
         res = list(ex.map(run, tasks))
     wall = time.perf_counter() - t0
-    return sum(r[0] for r in res), wall, sum(r[1] for r in res)
+    done = sum(r[1] for r in res)
+    return sum(r[0] for r in res), wall, done, sum(len(t[1]) for t in tasks) - done
 
 
 def workload_config(desc: str, n_gpus: int) -> dict:
@@ -173,27 +186,30 @@ def cpu_threads() -> int:
 
 
 def run_reference(args, g, qs, desc):
-    """The oracle, as it stands, on the host cores: each step a bounded root sample."""
+    """The oracle, as it stands, on the host cores: every step times the same
+    fixed root sample (the one the GPU arm's cpu_baseline times)."""
+    from oracle import oracle
     threads = cpu_threads()
-    per_step = max(2.0, args.cpu_seconds / 2)
+    og = oracle.OracleGraph(g)
+    tasks = fixed_root_tasks(g, qs)
     for w in range(args.warmup):
-        oracle_sample(g, qs, per_step / 4, threads, seed=100 + w)
-    tot_m = tot_t = 0.0
-    tot_r = 0
+        oracle_sample(g, qs, threads, og, tasks[: max(1, len(tasks) // 8)])
+    vals, tot_m, tot_t, done, dropped = [], 0, 0.0, 0, 0
     for s in range(args.steps):
-        m, t, r = oracle_sample(g, qs, per_step, threads, seed=1000 + s)
-        tot_m += m
-        tot_t += t
-        tot_r += r
+        m, t, d, x = oracle_sample(g, qs, threads, og, tasks)
+        vals.append(m / t if t > 0 else 0.0)
+        tot_m, tot_t, done, dropped = tot_m + m, tot_t + t, d, x
     value = tot_m / tot_t if tot_t > 0 else 0.0
-    sample = (f"{tot_r} random root vertices (images of pattern node 0) spread over all "
-              f"{len(qs)} GFDs, about {per_step:.0f} s of oracle time per step")
+    sample = (f"fixed seeded sample: {ROOTS_PER_GFD} uniform root vertices (images of pattern node 0) per GFD, "
+              f"{len(qs)} GFDs, {done} roots searched to the end and {dropped} dropped at their "
+              f"task deadlines ({ROOTS_PER_TASK} roots, {TASK_DEADLINE_S:.0f} s each); "
+              f"{tot_m // max(1, args.steps)} matches per step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "config": workload_config(desc, args.gpus),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "spread": [min(vals), max(vals)] if vals else None},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -241,7 +257,6 @@ def main():
     ap.add_argument("--impl", default="gfd", choices=["gfd", "reference"])
     ap.add_argument("--workload", default="batched", choices=["batched", "mid", "tiny", "kg"])
     ap.add_argument("--scale", type=int, default=1, help="divide V and E (tests only)")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-non-induced", action="store_true",
                     help="skip the non-induced, X-pushdown and disconnected-pattern legs")
@@ -339,11 +354,34 @@ def main():
     step_ms = float(np.mean(times))
     step_ms_max, value = aggregate(step_ms, matches, dist, "cuda")
 
-    # algorithmic bytes of one enumeration launch: 8 B per work item (its index
-    # edge), one 32 B sector per edge probe, 8 B per stored partial match, one
-    # 32 B sector per attribute a literal reads per match, 4k B per violation
-    lit_bytes = sum(r.n_matches * 32 * literal_attrs(q) for r, q in zip(stats, qs))
-    b_alg = 8 * work + 32 * probes + 8 * rows + lit_bytes + sum(4 * r.k * r.n_violations for r in stats)
+    # counting pass (untimed): what the run's kernels read, for the byte model
+    cres = dg.validate_batch(qs, stream=stream, flags=flags | G.FLAG_COUNT, max_violations_hint=hint,
+                             frontier_budget_bytes=budget, kernel_variant=args.kernel_variant)
+    cnt = cres[0].counters()
+    nnz = sum(r.stat(G.STAT_INDEX) for r in cres)
+    V = g.n_vertices
+    out_bytes = sum(4 * r.k * r.n_violations for r in stats)
+    # The algorithmic-byte model of the hot path (filter, refinement, index,
+    # enumeration, literal check, output), with the counted quantities:
+    model = {
+        "filter": 10 * V * cnt["filter_keys"],                         # label + two offsets per vertex and key
+        "bitmaps": V // 8 * cnt["bitmaps"],                            # one candidate bitmap per compaction
+        "refine_index_scans": 8 * cnt["scan_cands"] + 5 * cnt["scan_entries"],  # offsets + (id, label) per entry
+        "index_lists": 8 * nnz,                                        # 2 x 4 B per index entry
+        "enum_index_reads": 4 * cnt["items"],                          # 4 B per entry of N_u
+        "enum_back_scans": 5 * cnt["back_deg"],                        # backward non-tree adjacency, 5 B per entry
+        "enum_negative_probes": 32 * cnt["neg_logd"],                  # one sector per binary-search step
+        "literal_reads": 32 * cnt["attr_reads"],                       # one sector per attribute read
+        "output": out_bytes,                                           # 4k B per violation
+    }
+    b_enum = (model["enum_index_reads"] + model["enum_back_scans"] + model["enum_negative_probes"]
+              + model["literal_reads"] + model["output"])
+    b_step = sum(model.values())
+    # what the kernel itself loads: 8 B per index entry (position, id), 16 B
+    # per signature, one sector per search step actually taken and per
+    # attribute, the partial matches written, the output
+    b_kernel = (8 * cnt["items"] + 16 * cnt["sig_loads"] + 32 * cnt["search_loads"] + 32 * cnt["attr_reads"]
+                + 8 * cnt["rows"] + out_bytes)
     t_enum = float(np.mean(enum_ms)) / 1000.0
     peaks = {}
     try:
@@ -351,12 +389,22 @@ def main():
     except Exception:
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = b_alg / t_enum / 1e9 if t_enum > 0 else 0.0
+    achieved = b_enum / t_enum / 1e9 if t_enum > 0 else 0.0
+    traffic = kernel_traffic(work)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if peak else None, "traffic": kernel_traffic(work),
+                "frac": achieved / peak if peak else None, "traffic": traffic,
                 "traffic_source": "ncu DRAM bytes per work item of a small capture x this launch's work items",
                 "kernel": "k_persistent (enumeration)", "launch_ms": t_enum * 1000,
-                "alg_bytes_per_launch": b_alg,
+                "model": "algorithmic bytes of the survey's byte model (index reads 4 B per N_u entry, "
+                         "backward non-tree adjacency 5 B per entry, 32 B per binary-search step of an absent-edge "
+                         "probe, 32 B per literal attribute read, 4k B per violation), counted by an untimed "
+                         "counting pass of the same launch",
+                "alg_bytes_per_launch": b_enum,
+                "dram_frac": (traffic / t_enum / 1e9 / peak) if (traffic and t_enum > 0 and peak) else None,
+                "kernel_loads_model": {"bytes": b_kernel, "frac": b_kernel / t_enum / 1e9 / peak if t_enum > 0 else None},
+                "step_model": {"bytes": b_step, "frac": b_step / (step_ms / 1000.0) / 1e9 / peak,
+                               "terms": model},
+                "counters": cnt,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
     # e2e: host GFDs in, sorted violation tuples back on the host
@@ -503,15 +551,24 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle
         threads = cpu_threads()
-        m, t, r = oracle_sample(g, qs, args.cpu_seconds, threads)
-        cpu = {"value": m / t if t > 0 else 0.0, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{r} random root vertices (images of pattern node 0) over all {len(qs)} GFDs, "
-                         f"{t:.1f} s wall"}
-        # the same at one thread (a shorter sample)
-        m1, t1, r1 = oracle_sample(g, qs, max(2.0, args.cpu_seconds / 4), 1, seed=11)
+        og = oracle.OracleGraph(g)
+        tasks = fixed_root_tasks(g, qs)
+        runs = [oracle_sample(g, qs, threads, og, tasks) for _ in range(2)]
+        vals = [m / t if t > 0 else 0.0 for (m, t, _, _) in runs]
+        m, t, d, x = runs[-1]
+        cpu = {"value": float(np.mean(vals)), "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"fixed seeded sample (the reference arm's): {ROOTS_PER_GFD} uniform root vertices "
+                         f"(images of pattern node 0) per GFD, {len(qs)} GFDs, {d} roots searched to the end, "
+                         f"{x} dropped at task deadlines ({ROOTS_PER_TASK} roots, {TASK_DEADLINE_S:.0f} s each), "
+                         f"{m} matches, {t:.1f} s wall",
+               "spread": [min(vals), max(vals)]}
+        # one thread, on the first eighth of the same sample
+        m1, t1, d1, _ = oracle_sample(g, qs, 1, og, tasks[: max(1, len(tasks) // 8)])
         cpu["one_thread"] = {"value": m1 / t1 if t1 > 0 else 0.0, "unit": UNIT, "cores": 1,
-                             "sample": f"{r1} random root vertices, {t1:.1f} s wall"}
+                             "sample": f"the first {len(tasks[: max(1, len(tasks) // 8)])} GFDs' roots of the "
+                                       f"same sample, {d1} roots, {t1:.1f} s wall"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -155,6 +155,11 @@ typedef struct {
                                        gfd_result_candidates (batch calls only;
                                        for inspection and tests) */
 
+#define GFD_FLAG_COUNT         0x80 /* counting pass: run the enumeration with an
+                                       instrumented kernel that counts what the
+                                       run reads (gfd_result_stat 7..22); the
+                                       results are unchanged, the run is slower */
+
 /* Tuning options; a NULL gfd_opts* or zero fields select the defaults. */
 typedef struct {
     int64_t frontier_budget_bytes; /* device bytes for partial-match buffers
@@ -255,7 +260,19 @@ double gfd_result_profile(const gfd_result *r, int32_t which, int64_t *launches)
 /* Statistics of the run: 0 supersteps, 1 work items expanded, 2 partial
  * matches written, 3 edge-lookup probes (whole run), 4 candidate-list entries
  * (sum over pattern nodes), 5 index entries, 6 number of extra runs made
- * because the violations of the call outgrew max_violations_hint. */
+ * because the violations of the call outgrew max_violations_hint. With
+ * GFD_FLAG_COUNT, 7..22 are the whole call's counters of what its kernels read:
+ * 7 work items (entries of the index lists N_u, Section III.B, or of another
+ * candidate list), 8 of them at the last level, 9 partial matches expanded,
+ * 10 sum over expanded partial matches of the adjacency lengths of their
+ * backward non-tree neighbours' images, 11 pair checks, 12 of them settled by
+ * the neighbourhood signature, 13 adjacency binary searches, 14 adjacency
+ * entries those searches read, 15 absent-edge checks, 16 sum over absent-edge
+ * checks of ceil(log2(d + 1)) (d the shorter adjacency list), 17 signature
+ * loads, 18 attribute loads of literal checks, 19 partial matches written,
+ * 20 candidates whose adjacency the refinement and index build scanned, 21
+ * adjacency entries they read, 22 the number of distinct filter keys (high 32
+ * bits) and of candidate bitmaps compacted (low 32 bits). */
 uint64_t gfd_result_stat(const gfd_result *r, int32_t which);
 /* The refined candidate list C(u) of pattern node `node` (Section III.B step
  * 1c: label and degree filter, then top-down and bottom-up refinement), kept by

@@ -34,9 +34,14 @@ FLAG_NO_GRAPH = 0x8
 FLAG_NON_INDUCED = 0x10
 FLAG_PUSH_X = 0x20
 FLAG_KEEP_CANDIDATES = 0x40
+FLAG_COUNT = 0x80
 
 PROF_FILTER, PROF_REFINE, PROF_INDEX, PROF_ENUM, PROF_SORT = range(5)
 STAT_STEPS, STAT_WORK, STAT_ROWS, STAT_PROBES, STAT_CANDIDATES, STAT_INDEX, STAT_RERUN = range(7)
+# counters of a GFD_FLAG_COUNT run (gfd_result_stat 7..21)
+COUNTERS = ("items", "items_last", "partials", "back_deg", "checks", "sig_settled", "searches",
+            "search_loads", "neg_checks", "neg_logd", "sig_loads", "attr_reads", "rows",
+            "scan_cands", "scan_entries", "keys_and_bitmaps")
 
 
 class GfdError(RuntimeError):
@@ -235,6 +240,13 @@ class Result:
 
     def stat(self, which: int) -> int:
         return int(_lib.gfd_result_stat(self._h, int(which)))
+
+    def counters(self) -> dict:
+        """The counters of a FLAG_COUNT run (whole call), by name."""
+        out = {name: self.stat(7 + i) for i, name in enumerate(COUNTERS)}
+        kb = out.pop("keys_and_bitmaps")
+        out["filter_keys"], out["bitmaps"] = kb >> 32, kb & 0xffffffff
+        return out
 
     def candidates(self, node: int) -> np.ndarray:
         """The refined candidate list of pattern node `node` (needs

@@ -136,7 +136,7 @@ double gfd_result_profile(const gfd_result* r, int32_t which, int64_t* launches)
 }
 
 uint64_t gfd_result_stat(const gfd_result* r, int32_t which) {
-    if (!r || which < 0 || which >= 7) return 0;
+    if (!r || which < 0 || which >= 7 + gfd::N_CNT) return 0;
     return r->stat[which];
 }
 

@@ -139,6 +139,28 @@ struct SlotState {
     uint64_t st_work, st_rows, st_probes, st_steps, st_cpi;
 };
 
+// Counters of the counting pass (GFD_FLAG_COUNT): what one run's kernels
+// read, per kind of access, for the algorithmic-byte model of the roofline.
+enum : int {
+    CNT_ITEMS = 0,     // work items expanded (entries of N_u or of a generator's list)
+    CNT_ITEMS_LAST,    // of them at the last level
+    CNT_PARTIALS,      // partial matches expanded (stored rows, and roots, with fan-out)
+    CNT_BACK_DEG,      // sum over expanded partial matches of the degrees (in the edge's
+                       // direction) of the images of their backward non-tree neighbours
+    CNT_CHECKS,        // pair checks made (required and absent edges)
+    CNT_SIG_SETTLED,   // of them settled by the neighbourhood signature
+    CNT_SEARCHES,      // binary searches of an adjacency list made
+    CNT_SEARCH_LOADS,  // adjacency entries those searches loaded
+    CNT_NEG_CHECKS,    // absent-edge checks made
+    CNT_NEG_LOGD,      // sum over absent-edge checks of ceil(log2(d + 1)), d the shorter list
+    CNT_SIG_LOADS,     // neighbourhood-signature loads
+    CNT_ATTR_READS,    // attribute loads of the literal checks
+    CNT_ROWS,          // partial matches written
+    CNT_SCAN_CANDS,    // refinement and index build: candidates whose adjacency was scanned
+    CNT_SCAN_ENTRIES,  // refinement and index build: adjacency entries read
+    N_CNT = 16
+};
+
 // Scheduler state shared by all slots of a run (device).
 struct Sched {
     int32_t n_slots;
@@ -162,6 +184,7 @@ struct Sched {
     uint64_t varena_used;
     int32_t vstride;
     int32_t pad2;
+    uint64_t cnt[N_CNT];      // counting pass only
     // next tile of the current step handed out to a warp that finished its
     // first one (tiles below the warp count go to warps by index); on its own
     // cache line, away from the fields every warp reads

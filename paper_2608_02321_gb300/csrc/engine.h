@@ -51,7 +51,7 @@ struct gfd_result {
     std::unique_ptr<int32_t[]> tuples;  // host copy made by gfd_result_tuples
     double prof_ms[5] = {0, 0, 0, 0, 0};
     int64_t prof_launch[5] = {0, 0, 0, 0, 0};
-    uint64_t stat[7] = {0, 0, 0, 0, 0, 0, 0};
+    uint64_t stat[7 + gfd::N_CNT] = {};   // gfd_result_stat: 7 run statistics, then the counters
     cudaStream_t stream = nullptr;
     bool has_cand = false;                      // GFD_FLAG_KEEP_CANDIDATES
     std::vector<std::vector<int32_t>> cand;     // refined candidate list per pattern node
@@ -114,6 +114,9 @@ struct HubQueue {
     unsigned long long* item;  // (job << 40) | (constraint << 32) | candidate index
     uint32_t* n;               // items queued (may exceed cap: only cap are stored)
     uint32_t cap;
+    // counting pass: [0] candidates whose adjacency was scanned, [1] adjacency
+    // entries read (null: not counting)
+    unsigned long long* scan;
 };
 
 // ---- index kernels (index.cu); each launch covers all jobs given
@@ -157,8 +160,10 @@ int launch_split(const SlotDesc* slots, const int32_t* arena, uint64_t n, int32_
 // 4 (128, >= 16), 5 (512, >= 3).
 // general: some slot has a pattern component that starts after level 0 or X
 // pushed down (the expansion compiled with those paths); else the leaner one.
+// count: the counting instantiation (persistent, general, 256 threads), which
+// also fills Sched::cnt; used untimed for the algorithmic-byte model.
 int enum_run(const EnumArgs& a, bool persistent, bool use_graph, int variant, bool general, cudaStream_t st,
-             cudaEvent_t ev0, cudaEvent_t ev1, int64_t* launches);
+             cudaEvent_t ev0, cudaEvent_t ev1, int64_t* launches, bool count = false);
 int variant_threads(int variant);
 constexpr int N_VARIANTS = 6;
 

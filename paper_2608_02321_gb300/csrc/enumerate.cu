@@ -49,10 +49,38 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     return t;
 }
 
+// Per-thread counters of the counting pass (empty unless COUNT), added into
+// Sched::cnt once per warp at the end of the expansion.
+template <bool COUNT>
+struct Counters {
+    __device__ __forceinline__ void add(int, uint64_t) {}
+    __device__ __forceinline__ uint32_t* loads() { return nullptr; }
+    __device__ __forceinline__ void flush(Sched*) {}
+};
+template <>
+struct Counters<true> {
+    uint64_t c[N_CNT] = {};
+    uint32_t search_loads = 0;
+    __device__ __forceinline__ void add(int i, uint64_t v) { c[i] += v; }
+    __device__ __forceinline__ uint32_t* loads() { return &search_loads; }
+    __device__ void flush(Sched* s) {
+        c[CNT_SEARCH_LOADS] += search_loads;
+        for (int i = 0; i < N_CNT; i++) {
+            uint64_t v = c[i];
+            for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+            if ((threadIdx.x & 31) == 0 && v) atomicAdd((unsigned long long*)&s->cnt[i], (unsigned long long)v);
+        }
+    }
+};
+
+__device__ __forceinline__ uint32_t ceil_log2_1(uint32_t d) { return 32 - __clz(d); }  // ceil(log2(d + 1))
+
 // Label of the data-graph edge a -> b, or NOEDGE: binary search in the shorter
-// of out(a) and in(b) (both sorted by neighbour id).
+// of out(a) and in(b) (both sorted by neighbour id). loads (counting pass
+// only, else null) accumulates the adjacency entries read.
 __device__ __forceinline__ int32_t edge_label(const DevGraph& g, uint32_t a, uint32_t a_out0, uint32_t a_out1,
-                                              uint32_t b, uint32_t b_in0, uint32_t b_in1) {
+                                              uint32_t b, uint32_t b_in0, uint32_t b_in1,
+                                              uint32_t* loads = nullptr) {
     const uint32_t* arr;
     uint32_t lo, hi, key;
     if (a_out1 - a_out0 <= b_in1 - b_in0) {
@@ -70,20 +98,25 @@ __device__ __forceinline__ int32_t edge_label(const DevGraph& g, uint32_t a, uin
     const uint32_t kk = key << g.lbits;
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
+        if (loads) ++*loads;
         if (__ldg(arr + mid) < kk) lo = mid + 1;
         else hi = mid;
     }
     if (lo < end) {
+        if (loads) ++*loads;
         const uint32_t p = __ldg(arr + lo);
         if ((p >> g.lbits) == key) return (int32_t)(p & g.lmask);
     }
     return NOEDGE;
 }
 
-__device__ __forceinline__ bool lit_holds(const DevGraph& g, const DevLit& L, const uint32_t* m) {
+__device__ __forceinline__ bool lit_holds(const DevGraph& g, const DevLit& L, const uint32_t* m,
+                                          uint32_t* reads = nullptr) {
+    if (reads) ++*reads;
     const int32_t va = __ldg(g.attrs + (uint64_t)L.a * g.n + m[L.xl]);
     if (va == GFD_ATTR_ABSENT) return false;
     if (L.kind == 0) return va == L.c;
+    if (reads) ++*reads;
     const int32_t vb = __ldg(g.attrs + (uint64_t)L.b * g.n + m[L.yl]);
     return vb != GFD_ATTR_ABSENT && va == vb;
 }
@@ -182,8 +215,10 @@ __device__ __forceinline__ uint64_t warp_excl_scan(uint64_t x, int lane, uint64_
 // GEN = false: the common case (connected patterns, X checked at the last
 // level only), compiled without the general paths so that it keeps its
 // registers; GEN = true adds component starts and X pushed down.
-template <bool GEN>
+template <bool GEN, bool COUNT>
 __device__ void expand_warps(const EnumArgs& A) {
+    Counters<COUNT> cn;
+    uint32_t attr_reads = 0;
     const int lane = threadIdx.x & 31;
     const uint64_t gwarp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -265,6 +300,8 @@ __device__ void expand_warps(const EnumArgs& A) {
                 cur = __shfl_sync(0xffffffffu, r, 31);
             }
             if (ok) {
+                cn.add(CNT_ITEMS, 1);
+                if (last) cn.add(CNT_ITEMS_LAST, 1);
                 if (k == 1) {
                     j = (int32_t)w;
                     v = (uint32_t)D->cand[0][j];
@@ -285,6 +322,19 @@ __device__ void expand_warps(const EnumArgs& A) {
                         ent = (uint64_t)(uint32_t)rowp[2 * (l + 1) + 1] + o;
                     }
                     int skip = -1;
+                    if (COUNT && o == 0) {
+                        // the row's first item: the partial match is expanded once;
+                        // a merge-based intersection would scan the adjacency of
+                        // each backward non-tree neighbour's image
+                        cn.add(CNT_PARTIALS, 1);
+                        uint64_t bd = 0;
+                        for (int c = 0; c < LP.nchk; c++) {
+                            if (LP.chk_exp[c] == EXP_NONE) continue;
+                            const uint32_t x = m[LP.chk_q[c]];
+                            bd += LP.chk_dir[c] ? g.in_off[x + 1] - g.in_off[x] : g.out_off[x + 1] - g.out_off[x];
+                        }
+                        cn.add(CNT_BACK_DEG, bd);
+                    }
                     if (choice == 0) {
                         // candidates from the index edges of the spanning-tree parent
                         const int2 e = __ldg(D->cpi_idx[i] + ent);
@@ -311,9 +361,15 @@ __device__ void expand_warps(const EnumArgs& A) {
                             const uint32_t xp = m[LP.par];
                             const ulonglong2 sg = __ldg(g.sig + v);
                             int32_t gl = NOEDGE;
-                            if (((LP.tdir ? sg.y : sg.x) >> sig_bit(xp)) & 1ull)
-                                gl = LP.tdir ? edge_label(g, xp, g.out_off[xp], g.out_off[xp + 1], v, g.in_off[v], g.in_off[v + 1])
-                                             : edge_label(g, v, g.out_off[v], g.out_off[v + 1], xp, g.in_off[xp], g.in_off[xp + 1]);
+                            cn.add(CNT_SIG_LOADS, 1);
+                            cn.add(CNT_CHECKS, 1);
+                            if (((LP.tdir ? sg.y : sg.x) >> sig_bit(xp)) & 1ull) {
+                                cn.add(CNT_SEARCHES, 1);
+                                gl = LP.tdir ? edge_label(g, xp, g.out_off[xp], g.out_off[xp + 1], v, g.in_off[v], g.in_off[v + 1], cn.loads())
+                                             : edge_label(g, v, g.out_off[v], g.out_off[v + 1], xp, g.in_off[xp], g.in_off[xp + 1], cn.loads());
+                            } else {
+                                cn.add(CNT_SIG_SETTLED, 1);
+                            }
                             probes++;
                             ok = exp_ok(LP.tlab, gl);
                         }
@@ -328,13 +384,25 @@ __device__ void expand_warps(const EnumArgs& A) {
                         const ulonglong2 sg = __ldg(g.sig + v);
                         const uint32_t vo0 = g.out_off[v], vo1 = g.out_off[v + 1];
                         const uint32_t vi0 = g.in_off[v], vi1 = g.in_off[v + 1];
+                        cn.add(CNT_SIG_LOADS, 1);
                         for (int c = 0; c < LP.nchk && ok; c++) {
                             if (c == skip) continue;
                             const uint32_t x = m[LP.chk_q[c]];
                             int32_t gl = NOEDGE;
+                            cn.add(CNT_CHECKS, 1);
+                            if (COUNT && LP.chk_exp[c] == EXP_NONE) {
+                                const uint32_t dv = LP.chk_dir[c] ? vo1 - vo0 : vi1 - vi0;
+                                const uint32_t dx = LP.chk_dir[c] ? g.in_off[x + 1] - g.in_off[x]
+                                                                  : g.out_off[x + 1] - g.out_off[x];
+                                cn.add(CNT_NEG_CHECKS, 1);
+                                cn.add(CNT_NEG_LOGD, ceil_log2_1(min(dv, dx)));
+                            }
                             if (((LP.chk_dir[c] ? sg.x : sg.y) >> sig_bit(x)) & 1ull) {
-                                if (LP.chk_dir[c]) gl = edge_label(g, v, vo0, vo1, x, g.in_off[x], g.in_off[x + 1]);
-                                else gl = edge_label(g, x, g.out_off[x], g.out_off[x + 1], v, vi0, vi1);
+                                cn.add(CNT_SEARCHES, 1);
+                                if (LP.chk_dir[c]) gl = edge_label(g, v, vo0, vo1, x, g.in_off[x], g.in_off[x + 1], cn.loads());
+                                else gl = edge_label(g, x, g.out_off[x], g.out_off[x + 1], v, vi0, vi1, cn.loads());
+                            } else {
+                                cn.add(CNT_SIG_SETTLED, 1);
                             }
                             probes++;
                             ok = exp_ok(LP.chk_exp[c], gl);
@@ -346,7 +414,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                 // level (before the last one; the last level checks its own below)
                 if (GEN && ok && D->push_x && !last)
                     for (int q = 0; q < D->nx && ok; q++)
-                        if (D->lit[q].lvl == i) ok = lit_holds(g, D->lit[q], m);
+                        if (D->lit[q].lvl == i) ok = lit_holds(g, D->lit[q], m, COUNT ? &attr_reads : nullptr);
             }
             if (last) {
                 // complete match: check the X literals of this level, count it
@@ -355,12 +423,13 @@ __device__ void expand_warps(const EnumArgs& A) {
                 if (ok) {
                     bool x_ok = true;
                     for (int q = 0; q < D->nx && x_ok; q++)
-                        if (!GEN || D->lit[q].lvl == i) x_ok = lit_holds(g, D->lit[q], m);
+                        if (!GEN || D->lit[q].lvl == i) x_ok = lit_holds(g, D->lit[q], m, COUNT ? &attr_reads : nullptr);
                     if (GEN) tile_matches += x_ok || !D->push_x;
                     else tile_matches++;
                     if (x_ok) {
                         bool y_ok = !D->y_false;
-                        for (int q = 0; q < D->ny && y_ok; q++) y_ok = lit_holds(g, D->lit[D->nx + q], m);
+                        for (int q = 0; q < D->ny && y_ok; q++)
+                            y_ok = lit_holds(g, D->lit[D->nx + q], m, COUNT ? &attr_reads : nullptr);
                         viol = !y_ok;
                     }
                 }
@@ -436,6 +505,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                     if (ok) {
                         const uint64_t row = (old >> ROW_SHIFT) + (excl >> ROW_SHIFT);
                         if (row < D->chunk) {
+                            cn.add(CNT_ROWS, 1);
                             const int nw = 2 * (i + 1) + 2;
                             int32_t* dst = D->rows[i] + row * nw;
                             for (int q = 0; q <= i; q++) dst[q] = (int32_t)m[q];
@@ -464,6 +534,10 @@ __device__ void expand_warps(const EnumArgs& A) {
     // probe statistics: one atomic per warp
     const unsigned long long p = __reduce_add_sync(0xffffffffu, (unsigned)min(probes, (uint64_t)0xffffffffu));
     if (lane == 0 && p) atomicAdd((unsigned long long*)&A.sched->probes, p);
+    if (COUNT) {
+        cn.add(CNT_ATTR_READS, attr_reads);
+        cn.flush(A.sched);
+    }
 }
 
 // Start the enumeration of a slot whose index is built: level 0 holds the root
@@ -580,7 +654,7 @@ __global__ void __launch_bounds__(CTRL_THREADS) k_control(EnumArgs A, int first)
 
 template <int NT, int MINB, bool GEN>
 __global__ void __launch_bounds__(NT, MINB) k_expand(EnumArgs A) {
-    expand_warps<GEN>(A);
+    expand_warps<GEN, false>(A);
 }
 
 // Bounded grid barrier (cooperative launch guarantees co-residency): the last
@@ -621,10 +695,10 @@ __device__ bool grid_barrier(Sched* s) {
     return ok_s != 0;
 }
 
-template <int NT, int MINB, bool GEN>
+template <int NT, int MINB, bool GEN, bool COUNT = false>
 __global__ void __launch_bounds__(NT, MINB) k_persistent(EnumArgs A) {
     for (;;) {
-        expand_warps<GEN>(A);
+        expand_warps<GEN, COUNT>(A);
         if (!grid_barrier(A.sched)) return;
         if (blockIdx.x == 0) control_step<NT>(A, false);
         if (!grid_barrier(A.sched)) return;
@@ -632,12 +706,12 @@ __global__ void __launch_bounds__(NT, MINB) k_persistent(EnumArgs A) {
     }
 }
 
-template <int NT, int MINB, bool GEN>
+template <int NT, int MINB, bool GEN, bool COUNT = false>
 int launch_persistent(const EnumArgs& a, cudaStream_t st, int64_t* launches) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<NT, MINB, GEN>, NT, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<NT, MINB, GEN, COUNT>, NT, 0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm < 1) {
         set_error(GFD_ERR_CUDA, "persistent enumeration kernel cannot be resident");
@@ -647,7 +721,8 @@ int launch_persistent(const EnumArgs& a, cudaStream_t st, int64_t* launches) {
     EnumArgs args = a;
     args.n_warps = grid * (NT / 32);
     void* params[] = {&args};
-    e = cudaLaunchCooperativeKernel((const void*)k_persistent<NT, MINB, GEN>, dim3(grid), dim3(NT), params, 0, st);
+    e = cudaLaunchCooperativeKernel((const void*)k_persistent<NT, MINB, GEN, COUNT>, dim3(grid), dim3(NT), params, 0,
+                                    st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel");
     if (launches) *launches += 1;
     return GFD_OK;
@@ -860,9 +935,10 @@ int enum_init(const EnumArgs& a, cudaStream_t st) {
 }
 
 int enum_run(const EnumArgs& a, bool persistent, bool use_graph, int variant, bool general, cudaStream_t st,
-             cudaEvent_t ev0, cudaEvent_t ev1, int64_t* launches) {
+             cudaEvent_t ev0, cudaEvent_t ev1, int64_t* launches, bool count) {
     if (ev0) cudaEventRecord(ev0, st);
-    const int rc = general ? run_any_variant<true>(a, persistent, use_graph, variant, st, launches)
+    const int rc = count     ? launch_persistent<256, 4, true, true>(a, st, launches)
+                 : general ? run_any_variant<true>(a, persistent, use_graph, variant, st, launches)
                            : run_any_variant<false>(a, persistent, use_graph, variant, st, launches);
     if (ev1) cudaEventRecord(ev1, st);
     return rc;

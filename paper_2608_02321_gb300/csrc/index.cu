@@ -186,6 +186,20 @@ __device__ __forceinline__ bool hub_push(const HubQueue& q, bool want, unsigned 
 
 __device__ __forceinline__ uint32_t hub_count(const HubQueue& q) { return min(*q.n, q.cap); }
 
+// Counting pass: add this thread's scanned candidates and adjacency entries to
+// the run's counters (all lanes of the warp call it; one atomic per warp).
+__device__ __forceinline__ void scan_flush(const HubQueue& q, uint64_t cands, uint64_t entries) {
+    if (!q.scan) return;
+    for (int d = 16; d >= 1; d >>= 1) {
+        cands += __shfl_xor_sync(0xffffffffu, cands, d);
+        entries += __shfl_xor_sync(0xffffffffu, entries, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (cands) atomicAdd(&q.scan[0], (unsigned long long)cands);
+        if (entries) atomicAdd(&q.scan[1], (unsigned long long)entries);
+    }
+}
+
 __device__ __forceinline__ void load_group(const uint32_t* adj, uint32_t e, uint32_t e1, uint32_t (&p)[UNROLL]) {
 #pragma unroll
     for (int t = 0; t < UNROLL; t++) p[t] = e + t < e1 ? __ldg(adj + e + t) : 0u;
@@ -194,6 +208,7 @@ __device__ __forceinline__ void load_group(const uint32_t* adj, uint32_t e, uint
 __global__ void k_scatter(DevGraph g, const ScatterJob* __restrict__ jobs, int njobs, HubQueue hq) {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
+    uint64_t sc = 0, se = 0;
     for (int j = 0; j < njobs; j++) {
         const ScatterJob J = jobs[j];
         const uint32_t n = *J.qcount;
@@ -210,6 +225,8 @@ __global__ void k_scatter(DevGraph g, const ScatterJob* __restrict__ jobs, int n
             }
             if (hub_push(hq, e1 - e0 > HUB_LIST, ((unsigned long long)j << 40) | a, lane)) e1 = e0;
             const bool is_long = e1 - e0 > SHORT_LIST;
+            sc += a < n && e1 > e0;
+            se += e1 - e0;
             if (!is_long)
                 for (uint32_t e = e0; e < e1; e += UNROLL) {
                     uint32_t p[UNROLL], f[UNROLL];
@@ -236,13 +253,15 @@ __global__ void k_scatter(DevGraph g, const ScatterJob* __restrict__ jobs, int n
             }
         }
     }
+    scan_flush(hq, sc, se);
 }
 
 // Does the list adj[e0, e1) hold a neighbour in bm with an allowed label? One
 // lane alone (short lists) or the whole warp (cooperative).
 __device__ __forceinline__ bool any_hit_serial(const DevGraph& g, const uint32_t* adj, uint32_t e0, uint32_t e1,
-                                               int32_t lab, const uint32_t* bm) {
+                                               int32_t lab, const uint32_t* bm, uint64_t& read) {
     for (uint32_t e = e0; e < e1; e += UNROLL) {
+        read += min((uint32_t)UNROLL, e1 - e);
         uint32_t p[UNROLL], w[UNROLL];
         load_group(adj, e, e1, p);
 #pragma unroll
@@ -257,8 +276,9 @@ __device__ __forceinline__ bool any_hit_serial(const DevGraph& g, const uint32_t
 }
 
 __device__ __forceinline__ bool any_hit_warp(const DevGraph& g, const uint32_t* adj, uint32_t e0, uint32_t e1,
-                                             int32_t lab, const uint32_t* bm, int lane) {
+                                             int32_t lab, const uint32_t* bm, int lane, uint64_t& read) {
     for (uint32_t b = e0; b < e1; b += 32) {
+        if (lane == 0) read += min(32u, e1 - b);
         const uint32_t e = b + lane;
         bool hit = false;
         if (e < e1) {
@@ -273,6 +293,7 @@ __device__ __forceinline__ bool any_hit_warp(const DevGraph& g, const uint32_t* 
 __global__ void k_prune(DevGraph g, const PruneJob* __restrict__ jobs, int njobs, HubQueue hq) {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
+    uint64_t sc = 0, se = 0;
     for (int j = 0; j < njobs; j++) {
         const PruneJob& J = jobs[j];
         const uint32_t n = *J.count;
@@ -296,23 +317,26 @@ __global__ void k_prune(DevGraph g, const PruneJob* __restrict__ jobs, int njobs
                 const bool queued = hub_push(hq, keep && e1 - e0 > HUB_LIST,
                                              ((unsigned long long)j << 40) | ((unsigned long long)c << 32) | a, lane);
                 const bool is_long = keep && !queued && e1 - e0 > SHORT_LIST;
-                if (keep && !queued && !is_long) keep = any_hit_serial(g, adj, e0, e1, J.con_lab[c], J.con_bm[c]);
+                sc += keep && !queued;
+                if (keep && !queued && !is_long) keep = any_hit_serial(g, adj, e0, e1, J.con_lab[c], J.con_bm[c], se);
                 for (uint32_t lm = __ballot_sync(0xffffffffu, is_long); lm; lm &= lm - 1) {
                     const int src = __ffs(lm) - 1;
                     const uint32_t b0 = __shfl_sync(0xffffffffu, e0, src), b1 = __shfl_sync(0xffffffffu, e1, src);
-                    const bool hit = any_hit_warp(g, adj, b0, b1, J.con_lab[c], J.con_bm[c], lane);
+                    const bool hit = any_hit_warp(g, adj, b0, b1, J.con_lab[c], J.con_bm[c], lane, se);
                     if (lane == src) keep = hit;
                 }
             }
             if (valid && !keep) atomicAnd(&J.bm[v >> 5], ~(1u << (v & 31)));
         }
     }
+    scan_flush(hq, sc, se);
 }
 
 // off[a] = number of children of parent candidate a
 __global__ void k_cpi_count(DevGraph g, const CpiJob* __restrict__ jobs, int njobs, HubQueue hq) {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
+    uint64_t sc = 0, se = 0;
     for (int j = 0; j < njobs; j++) {
         const CpiJob J = jobs[j];
         const uint32_t n = *J.pcount;
@@ -330,6 +354,8 @@ __global__ void k_cpi_count(DevGraph g, const CpiJob* __restrict__ jobs, int njo
             const bool queued = hub_push(hq, e1 - e0 > HUB_LIST, ((unsigned long long)j << 40) | a, lane);
             if (queued) e1 = e0;  // counted by a block later
             const bool is_long = e1 - e0 > SHORT_LIST;
+            sc += a < n && e1 > e0;
+            se += e1 - e0;
             uint32_t cnt = 0;
             if (!is_long)
                 for (uint32_t e = e0; e < e1; e += UNROLL) {
@@ -356,6 +382,7 @@ __global__ void k_cpi_count(DevGraph g, const CpiJob* __restrict__ jobs, int njo
             if (a < n && !queued) J.off[a] = cnt;
         }
     }
+    scan_flush(hq, sc, se);
 }
 
 // Exclusive scan of the per-candidate counts off[0..n) in place, off[n] =
@@ -431,6 +458,7 @@ __global__ void __launch_bounds__(COMPACT_THREADS) k_cpi_scan(const CpiJob* __re
 __global__ void k_cpi_fill(DevGraph g, const CpiJob* __restrict__ jobs, int njobs, HubQueue hq) {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
+    uint64_t sc = 0, se = 0;
     for (int j = 0; j < njobs; j++) {
         const CpiJob J = jobs[j];
         const uint32_t n = *J.pcount;
@@ -451,6 +479,8 @@ __global__ void k_cpi_fill(DevGraph g, const CpiJob* __restrict__ jobs, int njob
             }
             if (hub_push(hq, e1 - e0 > HUB_LIST, ((unsigned long long)j << 40) | a, lane)) e1 = e0;
             const bool is_long = e1 - e0 > SHORT_LIST;
+            sc += a < n && e1 > e0;
+            se += e1 - e0;
             if (!is_long)
                 for (uint32_t e = e0; e < e1; e += UNROLL) {
                     uint32_t p[UNROLL], w[UNROLL], rk[UNROLL];
@@ -499,6 +529,7 @@ __global__ void k_cpi_fill(DevGraph g, const CpiJob* __restrict__ jobs, int njob
             }
         }
     }
+    scan_flush(hq, sc, se);
 }
 
 // ---- hub lists, one block per queued (job, candidate[, constraint]) item
@@ -513,6 +544,10 @@ __global__ void __launch_bounds__(HUB_THREADS) k_scatter_hub(DevGraph g, const S
         const uint32_t* off = J.scan_out ? g.out_off : g.in_off;
         const uint32_t* adj = J.scan_out ? g.out_adj : g.in_adj;
         const uint32_t e1 = off[v + 1];
+        if (hq.scan && threadIdx.x == 0) {
+            atomicAdd(&hq.scan[0], 1ull);
+            atomicAdd(&hq.scan[1], (unsigned long long)(e1 - off[v]));
+        }
         for (uint32_t e = off[v] + threadIdx.x; e < e1; e += HUB_THREADS) {
             const uint32_t p = __ldg(adj + e);
             const uint32_t x = p >> g.lbits;
@@ -535,9 +570,11 @@ __global__ void __launch_bounds__(HUB_THREADS) k_prune_hub(DevGraph g, const Pru
         const uint32_t* adj = J.con_dir[c] ? g.out_adj : g.in_adj;
         const uint32_t e0 = off[v], e1 = off[v + 1];
         bool found = false;
+        uint32_t read = 0;
         for (uint32_t b = e0; b < e1; b += HUB_THREADS) {  // block-uniform bounds
             const uint32_t e = b + threadIdx.x;
             bool hit = false;
+            read += min((uint32_t)HUB_THREADS, e1 - b);
             if (e < e1) {
                 const uint32_t p = __ldg(adj + e);
                 hit = label_ok(J.con_lab[c], (int32_t)(p & g.lmask)) && bit_of(J.con_bm[c], p >> g.lbits);
@@ -546,6 +583,10 @@ __global__ void __launch_bounds__(HUB_THREADS) k_prune_hub(DevGraph g, const Pru
                 found = true;
                 break;
             }
+        }
+        if (hq.scan && threadIdx.x == 0) {
+            atomicAdd(&hq.scan[0], 1ull);
+            atomicAdd(&hq.scan[1], (unsigned long long)read);
         }
         if (!found && threadIdx.x == 0) atomicAnd(&J.bm[v >> 5], ~(1u << (v & 31)));
     }
@@ -565,6 +606,10 @@ __global__ void __launch_bounds__(HUB_THREADS) k_cpi_count_hub(DevGraph g, const
         const uint32_t* adj = J.out ? g.out_adj : g.in_adj;
         const uint32_t e1 = off[v + 1];
         uint32_t cnt = 0;
+        if (hq.scan && threadIdx.x == 0) {
+            atomicAdd(&hq.scan[0], 1ull);
+            atomicAdd(&hq.scan[1], (unsigned long long)(e1 - off[v]));
+        }
         for (uint32_t e = off[v] + threadIdx.x; e < e1; e += HUB_THREADS) {
             const uint32_t p = __ldg(adj + e);
             cnt += label_ok(J.lab, (int32_t)(p & g.lmask)) && bit_of(J.cbm, p >> g.lbits);
@@ -592,6 +637,10 @@ __global__ void __launch_bounds__(HUB_THREADS) k_cpi_fill_hub(DevGraph g, const 
         const uint32_t e0 = off[v], e1 = off[v + 1];
         const uint32_t o = J.off[a], oend = J.off[a + 1];
         uint32_t running = 0;
+        if (hq.scan && threadIdx.x == 0) {
+            atomicAdd(&hq.scan[0], 1ull);
+            atomicAdd(&hq.scan[1], (unsigned long long)(e1 - e0));
+        }
         for (uint32_t b = e0; b < e1; b += HUB_THREADS) {  // block-uniform bounds
             const uint32_t e = b + threadIdx.x;
             bool hit = false;

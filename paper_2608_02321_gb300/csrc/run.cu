@@ -617,10 +617,11 @@ int group_build(gfd_graph* g, Group* G, const Tables& T, bool refine, cudaStream
 }
 
 int group_launch(gfd_graph* g, Group* G, const Tables& T, cudaMemPool_t pool, cudaStream_t st, ProfEvents& prof,
-                 int64_t* launches) {
+                 int64_t* launches, bool count = false) {
     const DevGraph& dg = g->dg;
     uint8_t* base = G->base;
-    const HubQueue hq{(unsigned long long*)(base + G->o_hubq), (uint32_t*)(base + G->o_hubn), HUB_CAP};
+    const HubQueue hq{(unsigned long long*)(base + G->o_hubq), (uint32_t*)(base + G->o_hubn), HUB_CAP,
+                      count ? (unsigned long long*)&T.sched->cnt[CNT_SCAN_CANDS] : nullptr};
     prof.begin(PROF_FILTER, st);
     if (int rc = launch_filter(dg, (const FilterKey*)(base + G->o_keys), (int)G->keys.size(),
                                (uint32_t*)(base + G->o_keybm), st))
@@ -792,16 +793,17 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
     ProfEvents prof;
     if (int rc = prof.init((flags & GFD_FLAG_PROFILE) != 0)) return rc;
     int64_t launches[5] = {0, 0, 0, 0, 0};
-    const int lrc = group_launch(g, &G, T, pool, st, prof, launches);
+    const bool count = (flags & GFD_FLAG_COUNT) != 0;
+    const int lrc = group_launch(g, &G, T, pool, st, prof, launches, count);
     fr.p.push_back(G.cpi_base);
     if (lrc) return lrc;
     const EnumArgs A = enum_args(g, T);
     if (int rc = enum_init(A, st)) return rc;
     bool general = false;  // any slot needing the general expansion
     for (int s = 0; s < n; s++) general |= G.plans[s].push_x || G.plans[s].n_components > 1;
-    if (int rc = enum_run(A, persistent, use_graph, variant, general, st,
+    if (int rc = enum_run(A, persistent || count, use_graph, variant, general, st,
                           prof.on ? prof.ev[2 * PROF_ENUM] : nullptr, prof.on ? prof.ev[2 * PROF_ENUM + 1] : nullptr,
-                          &launches[PROF_ENUM]))
+                          &launches[PROF_ENUM], count))
         return rc;
     launches[PROF_ENUM] += 1;
 
@@ -876,6 +878,12 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
     for (int s = 0; s < n; s++) {
         gfd_result* r = make_result(G.plans[s], states[s], hs.steps, hs.probes, vbuf[s], st);
         vbuf[s] = nullptr;
+        if (count) {
+            for (int c = 0; c < N_CNT; c++) r->stat[7 + c] = hs.cnt[c];
+            // the last slot holds the host's figures: distinct filter keys and
+            // candidate bitmaps built (for the filter and bitmap bytes)
+            r->stat[7 + N_CNT - 1] = ((uint64_t)G.keys.size() << 32) | (uint64_t)G.compact_jobs.size();
+        }
         if (flags & GFD_FLAG_KEEP_CANDIDATES) {
             r->cand = std::move(kept[s]);
             r->has_cand = true;
