@@ -157,7 +157,7 @@ typedef struct {
 
 #define GFD_FLAG_COUNT         0x80 /* counting pass: run the enumeration with an
                                        instrumented kernel that counts what the
-                                       run reads (gfd_result_stat 7..22); the
+                                       run reads (gfd_result_stat 7..24); the
                                        results are unchanged, the run is slower */
 
 /* Tuning options; a NULL gfd_opts* or zero fields select the defaults. */
@@ -175,7 +175,7 @@ typedef struct {
                                       choice (gfd_autotune) or the default;
                                       1..6 = a fixed variant (threads per block
                                       and minimum resident blocks per SM:
-                                      256/4, 256/6, 256/8, 128/12, 128/16, 512/3) */
+                                      256/4, 256/6, 256/8, 128/12, 256/5, 512/3) */
     int64_t max_violations_hint;   /* violations the run stores before it must
                                       run again with exactly enough room (all
                                       GFDs of a call together) */
@@ -261,7 +261,7 @@ double gfd_result_profile(const gfd_result *r, int32_t which, int64_t *launches)
  * matches written, 3 edge-lookup probes (whole run), 4 candidate-list entries
  * (sum over pattern nodes), 5 index entries, 6 number of extra runs made
  * because the violations of the call outgrew max_violations_hint. With
- * GFD_FLAG_COUNT, 7..22 are the whole call's counters of what its kernels read:
+ * GFD_FLAG_COUNT, 7..24 are the whole call's counters of what its kernels read:
  * 7 work items (entries of the index lists N_u, Section III.B, or of another
  * candidate list), 8 of them at the last level, 9 partial matches expanded,
  * 10 sum over expanded partial matches of the adjacency lengths of their
@@ -271,8 +271,10 @@ double gfd_result_profile(const gfd_result *r, int32_t which, int64_t *launches)
  * checks of ceil(log2(d + 1)) (d the shorter adjacency list), 17 signature
  * loads, 18 attribute loads of literal checks, 19 partial matches written,
  * 20 candidates whose adjacency the refinement and index build scanned, 21
- * adjacency entries they read, 22 the number of distinct filter keys (high 32
- * bits) and of candidate bitmaps compacted (low 32 bits). */
+ * adjacency entries they read, 22 warp iterations of the expansion, 23 sum over
+ * them of the largest number of search loads one lane made, 24 the number of
+ * distinct filter keys (high 32 bits) and of candidate bitmaps compacted (low
+ * 32 bits). */
 uint64_t gfd_result_stat(const gfd_result *r, int32_t which);
 /* The refined candidate list C(u) of pattern node `node` (Section III.B step
  * 1c: label and degree filter, then top-down and bottom-up refinement), kept by

@@ -74,6 +74,10 @@ struct FilterKey {
     int32_t attr_c[KEY_ATTRS];
 };
 
+// ints of a stored partial match of level l (l+1 ids, l+1 candidate positions,
+// generator, index base), padded to a multiple of 16 bytes for vector loads
+__host__ __device__ constexpr int row_width(int l) { return (2 * (l + 1) + 2 + 3) & ~3; }
+
 struct LevelPlan {
     int8_t u;          // pattern node matched at this level
     int8_t par;        // level of its spanning-tree parent (-1 at level 0)
@@ -82,11 +86,13 @@ struct LevelPlan {
     int8_t ngen;       // number of alternative candidate generators in gen
     int8_t gen[3];     // chk entries (required, not the tree parent) whose other
                        // end's adjacency may generate the candidates instead
+    int8_t nreq;       // chk entries [0, nreq) are required edges, the rest absent
     int32_t tlab;      // tree edge label or GFD_WILDCARD
     uint32_t inj;      // bit q: v must differ from the vertex at level q
     int8_t chk_q[2 * MAXK];   // earlier level of each pair check
     int8_t chk_dir[2 * MAXK]; // 1: edge u -> node(q), 0: node(q) -> u
     int16_t chk_exp[2 * MAXK];// expectation (EXP_NONE / EXP_ANY / label)
+    uint32_t chk_w[2 * MAXK]; // the same packed: q | dir << 4 | (uint16_t)exp << 16
 };
 
 struct DevLit {
@@ -158,7 +164,11 @@ enum : int {
     CNT_ROWS,          // partial matches written
     CNT_SCAN_CANDS,    // refinement and index build: candidates whose adjacency was scanned
     CNT_SCAN_ENTRIES,  // refinement and index build: adjacency entries read
-    N_CNT = 16
+    CNT_ITERS,         // warp iterations of the expansion (32 work items each at most)
+    CNT_ITER_MAX_LOADS,// sum over warp iterations of the largest number of search
+                       // loads one lane made (the warp waits for its slowest lane)
+    CNT_HOST,          // filled by the host: distinct filter keys << 32 | bitmaps
+    N_CNT = 18
 };
 
 // Scheduler state shared by all slots of a run (device).

@@ -157,7 +157,7 @@ int launch_split(const SlotDesc* slots, const int32_t* arena, uint64_t n, int32_
 // Runs supersteps until every slot is finished. persistent: one cooperative
 // launch; else a host loop (optionally captured into CUDA graphs). variant:
 // 0 (256 threads, >= 4 blocks/SM), 1 (256, >= 6), 2 (256, >= 8), 3 (128, >= 12),
-// 4 (128, >= 16), 5 (512, >= 3).
+// 4 (256, >= 5), 5 (512, >= 3).
 // general: some slot has a pattern component that starts after level 0 or X
 // pushed down (the expansion compiled with those paths); else the leaner one.
 // count: the counting instantiation (persistent, general, 256 threads), which

@@ -55,16 +55,26 @@ template <bool COUNT>
 struct Counters {
     __device__ __forceinline__ void add(int, uint64_t) {}
     __device__ __forceinline__ uint32_t* loads() { return nullptr; }
+    __device__ __forceinline__ void iteration() {}
     __device__ __forceinline__ void flush(Sched*) {}
 };
 template <>
 struct Counters<true> {
     uint64_t c[N_CNT] = {};
-    uint32_t search_loads = 0;
+    uint32_t search_loads = 0;  // of the current warp iteration
     __device__ __forceinline__ void add(int i, uint64_t v) { c[i] += v; }
     __device__ __forceinline__ uint32_t* loads() { return &search_loads; }
-    __device__ void flush(Sched* s) {
+    // end of a warp iteration (all lanes): the slowest lane's search loads
+    __device__ __forceinline__ void iteration() {
+        const uint32_t mx = __reduce_max_sync(0xffffffffu, search_loads);
+        if ((threadIdx.x & 31) == 0) {
+            c[CNT_ITERS] += 1;
+            c[CNT_ITER_MAX_LOADS] += mx;
+        }
         c[CNT_SEARCH_LOADS] += search_loads;
+        search_loads = 0;
+    }
+    __device__ void flush(Sched* s) {
         for (int i = 0; i < N_CNT; i++) {
             uint64_t v = c[i];
             for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
@@ -110,14 +120,15 @@ __device__ __forceinline__ int32_t edge_label(const DevGraph& g, uint32_t a, uin
     return NOEDGE;
 }
 
+// m: the partial match in shared memory, level q at m[32 q] (one column per lane)
 __device__ __forceinline__ bool lit_holds(const DevGraph& g, const DevLit& L, const uint32_t* m,
                                           uint32_t* reads = nullptr) {
     if (reads) ++*reads;
-    const int32_t va = __ldg(g.attrs + (uint64_t)L.a * g.n + m[L.xl]);
+    const int32_t va = __ldg(g.attrs + (uint64_t)L.a * g.n + m[L.xl << 5]);
     if (va == GFD_ATTR_ABSENT) return false;
     if (L.kind == 0) return va == L.c;
     if (reads) ++*reads;
-    const int32_t vb = __ldg(g.attrs + (uint64_t)L.b * g.n + m[L.yl]);
+    const int32_t vb = __ldg(g.attrs + (uint64_t)L.b * g.n + m[L.yl << 5]);
     return vb != GFD_ATTR_ABSENT && va == vb;
 }
 
@@ -215,11 +226,18 @@ __device__ __forceinline__ uint64_t warp_excl_scan(uint64_t x, int lane, uint64_
 // GEN = false: the common case (connected patterns, X checked at the last
 // level only), compiled without the general paths so that it keeps its
 // registers; GEN = true adds component starts and X pushed down.
-template <bool GEN, bool COUNT>
+template <int NT, bool GEN, bool COUNT>
 __device__ void expand_warps(const EnumArgs& A) {
+    // Per warp in shared memory: the lanes' partial matches (level q of lane t
+    // at [32 q + t], so the lanes' dynamically indexed reads hit distinct
+    // banks) and the current tile's pair checks, packed.
+    __shared__ uint32_t s_m[NT / 32][MAXK * 32];
+    __shared__ uint32_t s_chk[NT / 32][2 * MAXK];
     Counters<COUNT> cn;
     uint32_t attr_reads = 0;
     const int lane = threadIdx.x & 31;
+    uint32_t* const m = &s_m[threadIdx.x >> 5][lane];
+    uint32_t* const cw = s_chk[threadIdx.x >> 5];
     const uint64_t gwarp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const DevGraph& g = A.g;
@@ -238,12 +256,16 @@ __device__ void expand_warps(const EnumArgs& A) {
         const uint64_t wb = __ldcg((const unsigned long long*)&S->cb) + (t - __ldcg(A.tile_base + s)) * tile;
         const uint64_t we = min(wb + tile, (uint64_t)__ldcg((const unsigned long long*)&S->ce));
         const LevelPlan& LP = D->lv[i];
+        const int nchk = LP.nchk;
+        __syncwarp();  // the previous tile's checks are no longer read
+        if (lane < nchk) cw[lane] = LP.chk_w[lane];
+        __syncwarp();
         const uint32_t* S0 = i > 0 ? D->cpi_off[i] : nullptr;
         const uint64_t* Sl = l >= 1 ? D->wpre[l] : nullptr;
         const int32_t* rows_l = l >= 1 ? D->rows[l] : nullptr;
         const uint64_t nrows = k == 1 ? 0 : (l == 0 ? (uint64_t)S->ncand[0]
                                                     : (uint64_t)__ldcg((const unsigned long long*)&S->nrows[l]));
-        const int rw = 2 * (l + 1) + 2;  // row width at level l: ids, positions, generator, index base
+        const int rw = row_width(l);  // ints per row at level l: ids, positions, generator, index base
         // level 1 starts a component: root r's items are [r c1, (r+1) c1)
         const bool list1 = GEN && k > 1 && l == 0 && LP.par < 0;
         const uint64_t c1 = list1 ? (uint64_t)S->ncand[1] : 0;
@@ -265,7 +287,6 @@ __device__ void expand_warps(const EnumArgs& A) {
         for (uint64_t w0 = wb; w0 < we; w0 += 32) {
             const uint64_t w = w0 + lane;
             bool ok = w < we;
-            uint32_t m[MAXK];
             uint32_t v = 0;
             int32_t j = 0;
             const int32_t* rowp = nullptr;
@@ -316,10 +337,21 @@ __device__ void expand_warps(const EnumArgs& A) {
                         choice = list1 ? GEN_LIST : 0;
                         m[0] = (uint32_t)D->cand[0][r];
                     } else {
+                        // the row's ids in 16-byte loads (rows are padded to 16 B;
+                        // m has room for the last group), generator and index base
+                        // in one 8-byte load
                         rowp = rows_l + (uint64_t)r * rw;
-                        for (int q = 0; q <= l; q++) m[q] = (uint32_t)rowp[q];
-                        choice = rowp[2 * (l + 1)];
-                        ent = (uint64_t)(uint32_t)rowp[2 * (l + 1) + 1] + o;
+                        const int4* r4 = reinterpret_cast<const int4*>(rowp);
+                        for (int q = 0; q <= l; q += 4) {
+                            const int4 t4 = r4[q >> 2];
+                            m[q << 5] = (uint32_t)t4.x;
+                            m[(q + 1) << 5] = (uint32_t)t4.y;
+                            m[(q + 2) << 5] = (uint32_t)t4.z;
+                            m[(q + 3) << 5] = (uint32_t)t4.w;
+                        }
+                        const int2 gb = *reinterpret_cast<const int2*>(rowp + 2 * (l + 1));
+                        choice = gb.x;
+                        ent = (uint64_t)(uint32_t)gb.y + o;
                     }
                     int skip = -1;
                     if (COUNT && o == 0) {
@@ -328,9 +360,9 @@ __device__ void expand_warps(const EnumArgs& A) {
                         // each backward non-tree neighbour's image
                         cn.add(CNT_PARTIALS, 1);
                         uint64_t bd = 0;
-                        for (int c = 0; c < LP.nchk; c++) {
+                        for (int c = 0; c < nchk; c++) {
                             if (LP.chk_exp[c] == EXP_NONE) continue;
-                            const uint32_t x = m[LP.chk_q[c]];
+                            const uint32_t x = m[LP.chk_q[c] << 5];
                             bd += LP.chk_dir[c] ? g.in_off[x + 1] - g.in_off[x] : g.out_off[x + 1] - g.out_off[x];
                         }
                         cn.add(CNT_BACK_DEG, bd);
@@ -350,7 +382,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                         // C(u) and probe the spanning-tree edge instead
                         const int cg = LP.gen[choice - 1];
                         skip = cg;
-                        const uint32_t x = m[LP.chk_q[cg]];
+                        const uint32_t x = m[LP.chk_q[cg] << 5];
                         const uint32_t p = LP.chk_dir[cg] ? __ldg(g.in_adj + __ldg(g.in_off + x) + o)
                                                           : __ldg(g.out_adj + __ldg(g.out_off + x) + o);
                         v = p >> g.lbits;
@@ -358,7 +390,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                              ((__ldg(D->bm[i] + (v >> 5)) >> (v & 31)) & 1u);
                         if (ok) {
                             j = cand_rank(D->bm[i], D->rank[i], v);
-                            const uint32_t xp = m[LP.par];
+                            const uint32_t xp = m[LP.par << 5];
                             const ulonglong2 sg = __ldg(g.sig + v);
                             int32_t gl = NOEDGE;
                             cn.add(CNT_SIG_LOADS, 1);
@@ -376,40 +408,43 @@ __device__ void expand_warps(const EnumArgs& A) {
                     }
                     // injectivity
                     for (int q = 0; q <= l && ok; q++)
-                        if (((LP.inj >> q) & 1u) && m[q] == v) ok = false;
-                    // every other pattern pair, both directions (required edges first)
-                    if (ok && LP.nchk > 0) {
-                        // v's signatures settle most pairs (absent edges) without
-                        // a search; the rest search the shorter adjacency list
+                        if (((LP.inj >> q) & 1u) && m[q << 5] == v) ok = false;
+                    // every other pattern pair, both directions (required edges
+                    // first): v's neighbourhood signatures settle most pairs (a
+                    // clear bit proves the edge absent); the rest search the
+                    // shorter adjacency list
+                    if (ok && nchk > 0) {
                         const ulonglong2 sg = __ldg(g.sig + v);
-                        const uint32_t vo0 = g.out_off[v], vo1 = g.out_off[v + 1];
-                        const uint32_t vi0 = g.in_off[v], vi1 = g.in_off[v + 1];
                         cn.add(CNT_SIG_LOADS, 1);
-                        for (int c = 0; c < LP.nchk && ok; c++) {
+                        for (int c = 0; c < nchk && ok; c++) {
                             if (c == skip) continue;
-                            const uint32_t x = m[LP.chk_q[c]];
+                            const uint32_t wd = cw[c];
+                            const uint32_t x = m[(wd & 15u) << 5];
+                            const bool out = (wd >> 4) & 1u;
+                            const int32_t ex = (int32_t)(int16_t)(wd >> 16);
                             int32_t gl = NOEDGE;
                             cn.add(CNT_CHECKS, 1);
-                            if (COUNT && LP.chk_exp[c] == EXP_NONE) {
-                                const uint32_t dv = LP.chk_dir[c] ? vo1 - vo0 : vi1 - vi0;
-                                const uint32_t dx = LP.chk_dir[c] ? g.in_off[x + 1] - g.in_off[x]
-                                                                  : g.out_off[x + 1] - g.out_off[x];
+                            if (COUNT && ex == EXP_NONE) {
+                                const uint32_t dv = out ? g.out_off[v + 1] - g.out_off[v] : g.in_off[v + 1] - g.in_off[v];
+                                const uint32_t dx = out ? g.in_off[x + 1] - g.in_off[x] : g.out_off[x + 1] - g.out_off[x];
                                 cn.add(CNT_NEG_CHECKS, 1);
                                 cn.add(CNT_NEG_LOGD, ceil_log2_1(min(dv, dx)));
                             }
-                            if (((LP.chk_dir[c] ? sg.x : sg.y) >> sig_bit(x)) & 1ull) {
+                            if (((out ? sg.x : sg.y) >> sig_bit(x)) & 1ull) {
                                 cn.add(CNT_SEARCHES, 1);
-                                if (LP.chk_dir[c]) gl = edge_label(g, v, vo0, vo1, x, g.in_off[x], g.in_off[x + 1], cn.loads());
-                                else gl = edge_label(g, x, g.out_off[x], g.out_off[x + 1], v, vi0, vi1, cn.loads());
+                                gl = out ? edge_label(g, v, g.out_off[v], g.out_off[v + 1], x, g.in_off[x], g.in_off[x + 1],
+                                                      cn.loads())
+                                         : edge_label(g, x, g.out_off[x], g.out_off[x + 1], v, g.in_off[v], g.in_off[v + 1],
+                                                      cn.loads());
                             } else {
                                 cn.add(CNT_SIG_SETTLED, 1);
                             }
                             probes++;
-                            ok = exp_ok(LP.chk_exp[c], gl);
+                            ok = exp_ok(ex, gl);
                         }
                     }
                 }
-                m[i] = v;
+                m[i << 5] = v;
                 // X pushed down: the X literals whose ends are matched at this
                 // level (before the last one; the last level checks its own below)
                 if (GEN && ok && D->push_x && !last)
@@ -448,13 +483,13 @@ __device__ void expand_warps(const EnumArgs& A) {
                             // the slot's own buffer: tuples in pattern-node order
                             if (idx < D->viol_cap) {
                                 int32_t* out = D->viol + idx * k;
-                                for (int q = 0; q < k; q++) out[D->order[q]] = (int32_t)m[q];
+                                for (int q = 0; q < k; q++) out[D->order[q]] = (int32_t)m[q << 5];
                             }
                         } else if (idx < A.sched->varena_cap) {
                             // the run's arena: [slot, tuple in pattern-node order]
                             int32_t* rec = A.sched->varena + idx * A.sched->vstride;
                             rec[0] = s;
-                            for (int q = 0; q < k; q++) rec[1 + D->order[q]] = (int32_t)m[q];
+                            for (int q = 0; q < k; q++) rec[1 + D->order[q]] = (int32_t)m[q << 5];
                         }
                     }
                 }
@@ -480,7 +515,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                     }
                     for (int q = 0; q < L2.ngen; q++) {
                         const int cg = L2.gen[q];
-                        const uint32_t x = m[L2.chk_q[cg]];
+                        const uint32_t x = m[L2.chk_q[cg] << 5];
                         const uint32_t d = L2.chk_dir[cg] ? __ldg(g.in_off + x + 1) - __ldg(g.in_off + x)
                                                           : __ldg(g.out_off + x + 1) - __ldg(g.out_off + x);
                         if (d < fo) {
@@ -506,9 +541,9 @@ __device__ void expand_warps(const EnumArgs& A) {
                         const uint64_t row = (old >> ROW_SHIFT) + (excl >> ROW_SHIFT);
                         if (row < D->chunk) {
                             cn.add(CNT_ROWS, 1);
-                            const int nw = 2 * (i + 1) + 2;
+                            const int nw = row_width(i);
                             int32_t* dst = D->rows[i] + row * nw;
-                            for (int q = 0; q <= i; q++) dst[q] = (int32_t)m[q];
+                            for (int q = 0; q <= i; q++) dst[q] = (int32_t)m[q << 5];
                             if (l == 0) {
                                 dst[i + 1] = (int32_t)r;
                             } else {
@@ -522,6 +557,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                     }
                 }
             }
+            cn.iteration();
         }
         if (last) {
             const unsigned long long tm = __reduce_add_sync(0xffffffffu, (unsigned)tile_matches);
@@ -654,7 +690,7 @@ __global__ void __launch_bounds__(CTRL_THREADS) k_control(EnumArgs A, int first)
 
 template <int NT, int MINB, bool GEN>
 __global__ void __launch_bounds__(NT, MINB) k_expand(EnumArgs A) {
-    expand_warps<GEN, false>(A);
+    expand_warps<NT, GEN, false>(A);
 }
 
 // Bounded grid barrier (cooperative launch guarantees co-residency): the last
@@ -698,7 +734,7 @@ __device__ bool grid_barrier(Sched* s) {
 template <int NT, int MINB, bool GEN, bool COUNT = false>
 __global__ void __launch_bounds__(NT, MINB) k_persistent(EnumArgs A) {
     for (;;) {
-        expand_warps<GEN, COUNT>(A);
+        expand_warps<NT, GEN, COUNT>(A);
         if (!grid_barrier(A.sched)) return;
         if (blockIdx.x == 0) control_step<NT>(A, false);
         if (!grid_barrier(A.sched)) return;
@@ -891,7 +927,7 @@ int run_variant(const EnumArgs& a, bool persistent, bool use_graph, cudaStream_t
 // compiler must allow (which caps registers per thread).
 int variant_threads(int v) {
     switch (v) {
-        case 3: case 4: return 128;
+        case 3: return 128;
         case 5: return 512;
         default: return 256;
     }
@@ -905,7 +941,7 @@ int capture_steps(const EnumArgs& a, int variant, int steps, cudaStream_t st, cu
         case 1: return capture_steps_t<256, 6, GEN>(a, steps, st, graph, exec);
         case 2: return capture_steps_t<256, 8, GEN>(a, steps, st, graph, exec);
         case 3: return capture_steps_t<128, 12, GEN>(a, steps, st, graph, exec);
-        case 4: return capture_steps_t<128, 16, GEN>(a, steps, st, graph, exec);
+        case 4: return capture_steps_t<256, 5, GEN>(a, steps, st, graph, exec);
         case 5: return capture_steps_t<512, 3, GEN>(a, steps, st, graph, exec);
         default: return capture_steps_t<256, 4, GEN>(a, steps, st, graph, exec);
     }
@@ -920,7 +956,7 @@ int run_any_variant(const EnumArgs& a, bool persistent, bool use_graph, int vari
         case 1: return run_variant<256, 6, GEN>(a, persistent, use_graph, st, launches);
         case 2: return run_variant<256, 8, GEN>(a, persistent, use_graph, st, launches);
         case 3: return run_variant<128, 12, GEN>(a, persistent, use_graph, st, launches);
-        case 4: return run_variant<128, 16, GEN>(a, persistent, use_graph, st, launches);
+        case 4: return run_variant<256, 5, GEN>(a, persistent, use_graph, st, launches);
         case 5: return run_variant<512, 3, GEN>(a, persistent, use_graph, st, launches);
         default: return run_variant<256, 4, GEN>(a, persistent, use_graph, st, launches);
     }

@@ -188,8 +188,9 @@ __device__ __forceinline__ uint32_t hub_count(const HubQueue& q) { return min(*q
 
 // Counting pass: add this thread's scanned candidates and adjacency entries to
 // the run's counters (all lanes of the warp call it; one atomic per warp).
+template <bool COUNT>
 __device__ __forceinline__ void scan_flush(const HubQueue& q, uint64_t cands, uint64_t entries) {
-    if (!q.scan) return;
+    if (!COUNT || !q.scan) return;
     for (int d = 16; d >= 1; d >>= 1) {
         cands += __shfl_xor_sync(0xffffffffu, cands, d);
         entries += __shfl_xor_sync(0xffffffffu, entries, d);
@@ -205,6 +206,7 @@ __device__ __forceinline__ void load_group(const uint32_t* adj, uint32_t e, uint
     for (int t = 0; t < UNROLL; t++) p[t] = e + t < e1 ? __ldg(adj + e + t) : 0u;
 }
 
+template <bool COUNT>
 __global__ void k_scatter(DevGraph g, const ScatterJob* __restrict__ jobs, int njobs, HubQueue hq) {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
@@ -253,7 +255,7 @@ __global__ void k_scatter(DevGraph g, const ScatterJob* __restrict__ jobs, int n
             }
         }
     }
-    scan_flush(hq, sc, se);
+    scan_flush<COUNT>(hq, sc, se);
 }
 
 // Does the list adj[e0, e1) hold a neighbour in bm with an allowed label? One
@@ -290,6 +292,7 @@ __device__ __forceinline__ bool any_hit_warp(const DevGraph& g, const uint32_t* 
     return false;
 }
 
+template <bool COUNT>
 __global__ void k_prune(DevGraph g, const PruneJob* __restrict__ jobs, int njobs, HubQueue hq) {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
@@ -329,10 +332,11 @@ __global__ void k_prune(DevGraph g, const PruneJob* __restrict__ jobs, int njobs
             if (valid && !keep) atomicAnd(&J.bm[v >> 5], ~(1u << (v & 31)));
         }
     }
-    scan_flush(hq, sc, se);
+    scan_flush<COUNT>(hq, sc, se);
 }
 
 // off[a] = number of children of parent candidate a
+template <bool COUNT>
 __global__ void k_cpi_count(DevGraph g, const CpiJob* __restrict__ jobs, int njobs, HubQueue hq) {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
@@ -382,7 +386,7 @@ __global__ void k_cpi_count(DevGraph g, const CpiJob* __restrict__ jobs, int njo
             if (a < n && !queued) J.off[a] = cnt;
         }
     }
-    scan_flush(hq, sc, se);
+    scan_flush<COUNT>(hq, sc, se);
 }
 
 // Exclusive scan of the per-candidate counts off[0..n) in place, off[n] =
@@ -455,6 +459,7 @@ __global__ void __launch_bounds__(COMPACT_THREADS) k_cpi_scan(const CpiJob* __re
     }
 }
 
+template <bool COUNT>
 __global__ void k_cpi_fill(DevGraph g, const CpiJob* __restrict__ jobs, int njobs, HubQueue hq) {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
@@ -529,7 +534,7 @@ __global__ void k_cpi_fill(DevGraph g, const CpiJob* __restrict__ jobs, int njob
             }
         }
     }
-    scan_flush(hq, sc, se);
+    scan_flush<COUNT>(hq, sc, se);
 }
 
 // ---- hub lists, one block per queued (job, candidate[, constraint]) item
@@ -727,7 +732,8 @@ static int hub_reset(const HubQueue& hq, cudaStream_t st) {
 int launch_scatter(const DevGraph& g, const ScatterJob* d_jobs, int njobs, const HubQueue& hq, cudaStream_t st) {
     if (njobs <= 0) return GFD_OK;
     if (int rc = hub_reset(hq, st)) return rc;
-    k_scatter<<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    if (hq.scan) k_scatter<true><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    else k_scatter<false><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
     k_scatter_hub<<<HUB_GRID, HUB_THREADS, 0, st>>>(g, d_jobs, hq);
     return check_launch("k_scatter");
 }
@@ -735,7 +741,8 @@ int launch_scatter(const DevGraph& g, const ScatterJob* d_jobs, int njobs, const
 int launch_prune(const DevGraph& g, const PruneJob* d_jobs, int njobs, const HubQueue& hq, cudaStream_t st) {
     if (njobs <= 0) return GFD_OK;
     if (int rc = hub_reset(hq, st)) return rc;
-    k_prune<<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    if (hq.scan) k_prune<true><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    else k_prune<false><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
     k_prune_hub<<<HUB_GRID, HUB_THREADS, 0, st>>>(g, d_jobs, hq);
     return check_launch("k_prune");
 }
@@ -748,7 +755,8 @@ int launch_cpi_count(const DevGraph& g, const CpiJob* d_jobs, int njobs, uint32_
                      uint32_t* d_totals, const HubQueue& hq, cudaStream_t st) {
     if (njobs <= 0) return GFD_OK;
     if (int rc = hub_reset(hq, st)) return rc;
-    k_cpi_count<<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    if (hq.scan) k_cpi_count<true><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    else k_cpi_count<false><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
     k_cpi_count_hub<<<HUB_GRID, HUB_THREADS, 0, st>>>(g, d_jobs, hq);
     const int grid = (int)std::min<uint64_t>((uint64_t)njobs * nchunks, 152 * 4);
     k_cpi_sums<<<grid, COMPACT_THREADS, 0, st>>>(d_jobs, njobs, nchunks);
@@ -760,7 +768,8 @@ int launch_cpi_count(const DevGraph& g, const CpiJob* d_jobs, int njobs, uint32_
 int launch_cpi_fill(const DevGraph& g, const CpiJob* d_jobs, int njobs, const HubQueue& hq, cudaStream_t st) {
     if (njobs <= 0) return GFD_OK;
     if (int rc = hub_reset(hq, st)) return rc;
-    k_cpi_fill<<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    if (hq.scan) k_cpi_fill<true><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    else k_cpi_fill<false><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
     k_cpi_fill_hub<<<HUB_GRID, HUB_THREADS, 0, st>>>(g, d_jobs, hq);
     return check_launch("k_cpi_fill");
 }

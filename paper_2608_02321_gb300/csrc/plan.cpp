@@ -319,6 +319,11 @@ int make_plan(const gfd_gfd* phi, int32_t n_attrs, const PlanStats& stats, HostP
             }
         }
         L.nchk = (int8_t)n;
+        L.nreq = 0;
+        while (L.nreq < n && L.chk_exp[L.nreq] != EXP_NONE) L.nreq++;
+        for (int c = 0; c < n; c++)
+            L.chk_w[c] = (uint32_t)L.chk_q[c] | ((uint32_t)L.chk_dir[c] << 4) |
+                         ((uint32_t)(uint16_t)L.chk_exp[c] << 16);
         // alternative generators: required edges to earlier levels other than the
         // spanning-tree parent (the adjacency of their image bounds the candidates)
         L.ngen = 0;

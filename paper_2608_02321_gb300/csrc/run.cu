@@ -315,7 +315,7 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
         }
         for (size_t q = 0; q < P.lits.size(); q++) D.lit[q] = P.lits[q];
         uint64_t row_bytes = 0;
-        for (int l = 1; l <= P.k - 2; l++) row_bytes += 4ull * (2 * (l + 1) + 2) + 8;
+        for (int l = 1; l <= P.k - 2; l++) row_bytes += 4ull * row_width(l) + 8;
         uint64_t chunk = o && o->chunk_rows > 0 ? (uint64_t)o->chunk_rows
                                                 : (row_bytes ? (uint64_t)frontier_per_slot / row_bytes : (1ull << 24) - 1);
         if (strict_budget && !(o && o->chunk_rows > 0) && chunk < MIN_CHUNK) {
@@ -345,7 +345,7 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
             G->cpi_bound += 8ull * std::max<uint64_t>(1, D.cpi_cap[i]) + 256;
         }
         for (int l = 1; l <= P.k - 2; l++) {
-            F.rows[l] = L.take(4ull * (2 * (l + 1) + 2) * chunk);
+            F.rows[l] = L.take(4ull * row_width(l) * chunk);
             F.wpre[l] = L.take(8ull * chunk);
         }
     }
@@ -880,9 +880,9 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
         vbuf[s] = nullptr;
         if (count) {
             for (int c = 0; c < N_CNT; c++) r->stat[7 + c] = hs.cnt[c];
-            // the last slot holds the host's figures: distinct filter keys and
-            // candidate bitmaps built (for the filter and bitmap bytes)
-            r->stat[7 + N_CNT - 1] = ((uint64_t)G.keys.size() << 32) | (uint64_t)G.compact_jobs.size();
+            // the host's figures: distinct filter keys and candidate bitmaps
+            // built (for the filter and bitmap bytes)
+            r->stat[7 + CNT_HOST] = ((uint64_t)G.keys.size() << 32) | (uint64_t)G.compact_jobs.size();
         }
         if (flags & GFD_FLAG_KEEP_CANDIDATES) {
             r->cand = std::move(kept[s]);
