@@ -183,6 +183,13 @@ __device__ __forceinline__ uint32_t find_row_in(const uint64_t* S, uint32_t lo, 
     return lo;
 }
 
+// One half of a vertex's neighbourhood signature: 0 its out-neighbours, 1 its
+// in-neighbours. An edge a -> b needs both b's bit in a's out-signature and
+// a's bit in b's in-signature, so either clear bit proves it absent.
+__device__ __forceinline__ uint64_t sig_half(const DevGraph& g, uint32_t x, int half) {
+    return __ldg(reinterpret_cast<const unsigned long long*>(g.sig) + 2 * (uint64_t)x + half);
+}
+
 // position of v in the sorted candidate list of a level: O(1) from the bitmap
 // and its per-word popcount prefix
 __device__ __forceinline__ int32_t cand_rank(const uint32_t* bm, const uint32_t* rank, uint32_t v) {
@@ -354,6 +361,14 @@ __device__ void expand_warps(const EnumArgs& A) {
                         ent = (uint64_t)(uint32_t)gb.y + o;
                     }
                     int skip = -1;
+                    // the first pair check's earlier image is the same for all the
+                    // row's candidates: its signature half (the one that holds v
+                    // if the edge exists) is loaded while the candidate is fetched
+                    uint64_t sx0 = 0;
+                    if (nchk > 0) {
+                        const uint32_t w0c = cw[0];
+                        sx0 = sig_half(g, m[(w0c & 15u) << 5], (w0c >> 4) & 1u);
+                    }
                     if (COUNT && o == 0) {
                         // the row's first item: the partial match is expanded once;
                         // a merge-based intersection would scan the adjacency of
@@ -391,11 +406,17 @@ __device__ void expand_warps(const EnumArgs& A) {
                         if (ok) {
                             j = cand_rank(D->bm[i], D->rank[i], v);
                             const uint32_t xp = m[LP.par << 5];
-                            const ulonglong2 sg = __ldg(g.sig + v);
-                            int32_t gl = NOEDGE;
+                            // tree edge xp -> v (tdir 1) or v -> xp: the parent's
+                            // signature first, then v's
+                            bool maybe = (sig_half(g, xp, LP.tdir ? 0 : 1) >> sig_bit(v)) & 1ull;
                             cn.add(CNT_SIG_LOADS, 1);
+                            if (maybe) {
+                                maybe = (sig_half(g, v, LP.tdir ? 1 : 0) >> sig_bit(xp)) & 1ull;
+                                cn.add(CNT_SIG_LOADS, 1);
+                            }
+                            int32_t gl = NOEDGE;
                             cn.add(CNT_CHECKS, 1);
-                            if (((LP.tdir ? sg.y : sg.x) >> sig_bit(xp)) & 1ull) {
+                            if (maybe) {
                                 cn.add(CNT_SEARCHES, 1);
                                 gl = LP.tdir ? edge_label(g, xp, g.out_off[xp], g.out_off[xp + 1], v, g.in_off[v], g.in_off[v + 1], cn.loads())
                                              : edge_label(g, v, g.out_off[v], g.out_off[v + 1], xp, g.in_off[xp], g.in_off[xp + 1], cn.loads());
@@ -414,23 +435,39 @@ __device__ void expand_warps(const EnumArgs& A) {
                     // clear bit proves the edge absent); the rest search the
                     // shorter adjacency list
                     if (ok && nchk > 0) {
-                        const ulonglong2 sg = __ldg(g.sig + v);
-                        cn.add(CNT_SIG_LOADS, 1);
+                        const uint32_t bv = sig_bit(v);
+                        uint64_t svo = 0, svi = 0;  // v's signature, loaded when needed
+                        bool have_sv = false;
                         for (int c = 0; c < nchk && ok; c++) {
                             if (c == skip) continue;
                             const uint32_t wd = cw[c];
                             const uint32_t x = m[(wd & 15u) << 5];
-                            const bool out = (wd >> 4) & 1u;
+                            const bool out = (wd >> 4) & 1u;  // edge v -> x, else x -> v
                             const int32_t ex = (int32_t)(int16_t)(wd >> 16);
                             int32_t gl = NOEDGE;
                             cn.add(CNT_CHECKS, 1);
+                            // v's bit in x's signature (x's in-neighbours for v -> x),
+                            // then x's bit in v's: a clear bit proves the edge absent
+                            const uint64_t sx = c == 0 ? sx0 : sig_half(g, x, out ? 1 : 0);
+                            if (c != 0) cn.add(CNT_SIG_LOADS, 1);
+                            bool maybe = (sx >> bv) & 1ull;
+                            if (maybe) {
+                                if (!have_sv) {
+                                    const ulonglong2 sg = __ldg(g.sig + v);
+                                    svo = sg.x;
+                                    svi = sg.y;
+                                    have_sv = true;
+                                    cn.add(CNT_SIG_LOADS, 1);
+                                }
+                                maybe = ((out ? svo : svi) >> sig_bit(x)) & 1ull;
+                            }
                             if (COUNT && ex == EXP_NONE) {
                                 const uint32_t dv = out ? g.out_off[v + 1] - g.out_off[v] : g.in_off[v + 1] - g.in_off[v];
                                 const uint32_t dx = out ? g.in_off[x + 1] - g.in_off[x] : g.out_off[x + 1] - g.out_off[x];
                                 cn.add(CNT_NEG_CHECKS, 1);
                                 cn.add(CNT_NEG_LOGD, ceil_log2_1(min(dv, dx)));
                             }
-                            if (((out ? sg.x : sg.y) >> sig_bit(x)) & 1ull) {
+                            if (maybe) {
                                 cn.add(CNT_SEARCHES, 1);
                                 gl = out ? edge_label(g, v, g.out_off[v], g.out_off[v + 1], x, g.in_off[x], g.in_off[x + 1],
                                                       cn.loads())
@@ -537,21 +574,36 @@ __device__ void expand_warps(const EnumArgs& A) {
                             atomicExch(&S->err, DERR_COUNTER_OVERFLOW);
                     }
                     old = __shfl_sync(0xffffffffu, old, 0);
+                    // the warp's new partial matches take rows [row0, row0 + its
+                    // count) of the level's buffer, in lane order
                     if (ok) {
                         const uint64_t row = (old >> ROW_SHIFT) + (excl >> ROW_SHIFT);
                         if (row < D->chunk) {
                             cn.add(CNT_ROWS, 1);
+                            // the row (ids, positions, generator, index base,
+                            // padding) in 16-byte stores, four ints at a time
                             const int nw = row_width(i);
                             int32_t* dst = D->rows[i] + row * nw;
-                            for (int q = 0; q <= i; q++) dst[q] = (int32_t)m[q << 5];
-                            if (l == 0) {
-                                dst[i + 1] = (int32_t)r;
-                            } else {
-                                for (int q = 0; q <= l; q++) dst[i + 1 + q] = rowp[l + 1 + q];
+                            for (int t = 0; t < nw; t += 4) {
+                                int32_t e4[4];
+#pragma unroll
+                                for (int c = 0; c < 4; c++) {
+                                    const int idx = t + c;
+                                    int32_t val = 0;
+                                    if (idx <= i) {
+                                        val = (int32_t)m[idx << 5];
+                                    } else if (idx <= 2 * i + 1) {
+                                        const int q = idx - i - 1;
+                                        val = q == i ? j : (l == 0 ? (int32_t)r : rowp[l + 1 + q]);
+                                    } else if (idx == 2 * i + 2) {
+                                        val = gen;
+                                    } else if (idx == 2 * i + 3) {
+                                        val = (int32_t)nbase;
+                                    }
+                                    e4[c] = val;
+                                }
+                                *reinterpret_cast<int4*>(dst + t) = make_int4(e4[0], e4[1], e4[2], e4[3]);
                             }
-                            dst[i + 1 + i] = j;
-                            dst[2 * (i + 1)] = gen;
-                            dst[2 * (i + 1) + 1] = (int32_t)nbase;
                             D->wpre[i][row] = (old & WORK_MASK) + (excl & WORK_MASK);
                         }
                     }
