@@ -321,7 +321,14 @@ int gfd_session_next_result(gfd_session *s, int64_t *request_id, gfd_result **ou
  * gfd_session_step calls. Returns GFD_OK, or GFD_ERR_INVALID_ARG when the
  * session holds no request with that id (unknown, or already collected). */
 int gfd_session_cancel(gfd_session *s, int64_t request_id);
-/* Wait for the session's work, release it and any uncollected results. */
+/* Session statistics since creation, for monitoring: 0 host milliseconds spent
+ * admitting requests (planning, index builds), 1 milliseconds spent in
+ * enumeration rounds, 2 rounds run, 3 requests admitted, 4 admissions (groups
+ * of requests admitted together). 0 for NULL or another `which`. */
+double gfd_session_stat(const gfd_session *s, int32_t which);
+/* Wait for the session's work, release it and any uncollected results. Free
+ * every session of a graph before the graph: a session issues its work on the
+ * graph's stream unless opts->cuda_stream names another. */
 void gfd_session_free(gfd_session *s);
 
 /* Candidate filter of pattern node `node` of phi (its label, its out- and

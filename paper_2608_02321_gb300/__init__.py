@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 import threading
+import weakref
 
 import numpy as np
 
@@ -102,6 +103,7 @@ _SIGS = {
     "gfd_session_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "gfd_session_next_result": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_void_p)]),
     "gfd_session_cancel": (C.c_int, [C.c_void_p, C.c_int64]),
+    "gfd_session_stat": (C.c_double, [C.c_void_p, C.c_int32]),
     "gfd_session_free": (None, [C.c_void_p]),
     "gfd_node_candidates_noalloc": (C.c_int, [C.c_void_p, C.POINTER(gfd_gfd), C.c_int32, C.c_void_p,
                                               C.c_int64, C.POINTER(C.c_int64), C.c_void_p]),
@@ -291,9 +293,14 @@ class Graph:
         _check(lib.gfd_graph_load(C.byref(d), C.byref(o), C.byref(h)))
         del keep
         self._h = h
+        self._sessions = weakref.WeakSet()
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
+            # a session runs on the graph's stream: free it first (Python may
+            # finalise the two in either order when both are garbage at once)
+            for sess in list(getattr(self, "_sessions", ())):
+                sess.close()
             _lib.gfd_graph_free(self._h)
             self._h = None
 
@@ -339,11 +346,16 @@ class Session:
         h = C.c_void_p(None)
         _check(_lib.gfd_session_create(g._h, int(max_slots), C.byref(o), C.byref(h)))
         self._h = h
+        g._sessions.add(self)
 
-    def __del__(self):
+    def close(self):
+        """Release the session (gfd_session_free); later calls are errors."""
         if getattr(self, "_h", None) and _lib is not None:
             _lib.gfd_session_free(self._h)
             self._h = None
+
+    def __del__(self):
+        self.close()
 
     def submit(self, gfd) -> int:
         b = _GfdBuf(gfd)
@@ -364,6 +376,12 @@ class Session:
         """Drop a queued request, stop a running one or discard an uncollected
         result (gfd_session_cancel)."""
         _check(_lib.gfd_session_cancel(self._h, int(request_id)))
+
+    def stats(self) -> dict:
+        """Host time in admissions and in enumeration rounds, rounds run,
+        requests admitted, admissions (gfd_session_stat)."""
+        names = ("admit_ms", "round_ms", "rounds", "admitted", "admissions")
+        return {n: float(_lib.gfd_session_stat(self._h, i)) for i, n in enumerate(names)}
 
     def results(self):
         """All finished requests since the last call: [(request_id, Result)]."""

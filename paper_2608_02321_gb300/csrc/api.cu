@@ -155,6 +155,7 @@ int gfd_result_candidates(const gfd_result* r, int32_t node, const int32_t** lis
 void gfd_result_free(gfd_result* r) {
     if (!r) return;
     if (r->d_viol) cudaFree(r->d_viol);
+    cudaGetLastError();  // a failure here must not surface in a later, unrelated call
     delete r;
 }
 
@@ -175,6 +176,8 @@ int gfd_session_next_result(gfd_session* s, int64_t* request_id, gfd_result** ou
 }
 
 int gfd_session_cancel(gfd_session* s, int64_t request_id) { return gfd::session_cancel(s, request_id); }
+
+double gfd_session_stat(const gfd_session* s, int32_t which) { return gfd::session_stat(s, which); }
 
 void gfd_session_free(gfd_session* s) { gfd::session_free(s); }
 

@@ -178,6 +178,7 @@ int session_submit(gfd_session* s, const gfd_gfd* phi, int64_t* id);
 int session_step(gfd_session* s, int32_t* n_advanced, int32_t* n_running, int32_t* n_queued);
 int session_next_result(gfd_session* s, int64_t* id, gfd_result** out);
 int session_cancel(gfd_session* s, int64_t id);
+double session_stat(const gfd_session* s, int32_t which);
 int autotune(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opts* o, gfd_opts* best);
 // Sort the violation tuples on the device and copy them to dst (host memory,
 // n_viol * k ints); result_fetch does this into the result's own buffer.

@@ -407,6 +407,7 @@ void graph_free(gfd_graph* g) {
     if (g->eng) engine_free(g->eng);
     for (void* p : g->allocs) cudaFree(p);
     if (g->stream) cudaStreamDestroy(g->stream);
+    cudaGetLastError();  // a failure here must not surface in a later, unrelated call
     delete g;
 }
 

@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <cstdarg>
 #include <cstddef>
 #include <cstdio>
@@ -233,6 +234,7 @@ struct Group {
     std::vector<PruneJob> prune_jobs;
     std::vector<CpiJob> cpi_jobs;
     std::vector<Phase> phases;
+    std::vector<SlotState> state_img;  // host image of the cleared states (kept until copied)
     int live = 0;  // slots of this group still running (sessions)
 };
 
@@ -604,13 +606,19 @@ int group_build(gfd_graph* g, Group* G, const Tables& T, bool refine, cudaStream
     put(G->o_prn, G->prune_jobs.data(), sizeof(PruneJob) * G->prune_jobs.size());
     put(G->o_cpi, G->cpi_jobs.data(), sizeof(CpiJob) * G->cpi_jobs.size());
     GFD_CUDA(cudaMemcpyAsync(base + G->o_jobs, img.data(), img.size(), cudaMemcpyHostToDevice, st));
-    // descriptors into the slot tables (contiguous runs in one copy), states cleared
+    // descriptors into the slot tables (contiguous runs in one copy) and states
+    // cleared, idle (cur = -1): a serving session's running enumeration may
+    // read these slots' states while they are built, and must see them idle
+    // until they are started
+    G->state_img.assign(n, SlotState{});
+    for (auto& z : G->state_img) z.cur = -1;
     for (int s = 0; s < n;) {
         int e = s + 1;
         while (e < n && G->slot[e] == G->slot[e - 1] + 1) e++;
         GFD_CUDA(cudaMemcpyAsync(&T.desc[G->slot[s]], &G->descs[s], sizeof(SlotDesc) * (e - s),
                                  cudaMemcpyHostToDevice, st));
-        GFD_CUDA(cudaMemsetAsync(&T.state[G->slot[s]], 0, sizeof(SlotState) * (e - s), st));
+        GFD_CUDA(cudaMemcpyAsync(&T.state[G->slot[s]], &G->state_img[s], sizeof(SlotState) * (e - s),
+                                 cudaMemcpyHostToDevice, st));
         s = e;
     }
     return GFD_OK;
@@ -918,6 +926,7 @@ struct Request {
 
 struct SlotHost {
     bool busy = false;
+    bool started = false;  // its index is built and its enumeration started
     int64_t id = -1;
     std::shared_ptr<Group> group;
     int index = 0;  // position inside the group
@@ -933,7 +942,12 @@ struct SlotHost {
 struct gfd_session {
     gfd_graph* g = nullptr;
     gfd_opts opts{};
-    cudaStream_t st = nullptr;
+    cudaStream_t st = nullptr;        // enumeration rounds
+    cudaStream_t st_admit = nullptr;  // index builds of admitted requests
+    cudaEvent_t ev_admit = nullptr;   // an admission's index build is complete
+    gfd::SlotState* h_states = nullptr;  // pinned snapshot after a round
+    gfd::Sched* h_sched = nullptr;
+    int32_t* h_err = nullptr;
     cudaMemPool_t pool = nullptr;
     gfd::Tables T;
     int variant = 0;
@@ -948,6 +962,7 @@ struct gfd_session {
     int64_t next_id = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    double stat[5] = {0, 0, 0, 0, 0};  // gfd_session_stat
 };
 
 namespace gfd {
@@ -966,6 +981,11 @@ int session_create(gfd_graph* g, int32_t max_slots, const gfd_opts* o, gfd_sessi
     S->budget = default_budget(g, o);
     S->viol_cap = o && o->max_violations_hint > 0 ? (uint64_t)o->max_violations_hint : (1ull << 20);
     S->slots.resize(max_slots);
+    GFD_CUDA(cudaStreamCreateWithFlags(&S->st_admit, cudaStreamNonBlocking));
+    GFD_CUDA(cudaEventCreateWithFlags(&S->ev_admit, cudaEventDisableTiming));
+    GFD_CUDA(cudaMallocHost((void**)&S->h_states, sizeof(SlotState) * max_slots));
+    GFD_CUDA(cudaMallocHost((void**)&S->h_sched, sizeof(Sched)));
+    GFD_CUDA(cudaMallocHost((void**)&S->h_err, sizeof(int32_t)));
     if (int rc = get_pool(g, &S->pool)) return rc;
     if (int rc = tables_alloc(S->pool, max_slots, S->block_threads, pick_tile_iters(g, o), 0, 0, false, S->st, &S->T))
         return rc;
@@ -980,6 +1000,7 @@ int session_create(gfd_graph* g, int32_t max_slots, const gfd_opts* o, gfd_sessi
 
 void session_free(gfd_session* S) {
     if (!S) return;
+    if (S->st_admit) cudaStreamSynchronize(S->st_admit);
     cudaStreamSynchronize(S->st);
     for (auto& d : S->done) gfd_result_free(d.second);
     for (auto& sl : S->slots) {
@@ -994,6 +1015,12 @@ void session_free(gfd_session* S) {
     if (S->exec) cudaGraphExecDestroy(S->exec);
     if (S->graph) cudaGraphDestroy(S->graph);
     cudaStreamSynchronize(S->st);
+    if (S->h_states) cudaFreeHost(S->h_states);
+    if (S->h_sched) cudaFreeHost(S->h_sched);
+    if (S->h_err) cudaFreeHost(S->h_err);
+    if (S->ev_admit) cudaEventDestroy(S->ev_admit);
+    if (S->st_admit) cudaStreamDestroy(S->st_admit);
+    cudaGetLastError();  // a failure here must not surface in a later, unrelated call
     delete S;
 }
 
@@ -1055,16 +1082,21 @@ int session_admit(gfd_session* S) {
     }
     if (take.empty()) return GFD_OK;
     const int n = (int)take.size();
+    S->stat[3] += n;
+    S->stat[4] += 1;
+    // the index build runs on the admission stream, beside the round that the
+    // caller may have launched on the session stream
+    cudaStream_t sa = S->st_admit;
     auto G = std::make_shared<Group>();
     if (int rc = group_plan(S->g, phis.data(), n, &S->opts, per_slot, G.get())) return rc;
     void* wb = nullptr;
-    if (int rc = pool_alloc(S->pool, G->bytes, S->st, &wb, "request workspace")) return rc;
+    if (int rc = pool_alloc(S->pool, G->bytes, sa, &wb, "request workspace")) return rc;
     G->base = (uint8_t*)wb;
     G->slot.assign(free_slots.begin(), free_slots.begin() + n);
     S->used += (int64_t)G->bytes;
     for (int i = 0; i < n; i++) {
         void* vp = nullptr;
-        if (int rc = pool_alloc(S->pool, 4ull * G->plans[i].k * S->viol_cap, S->st, &vp, "violation buffer")) return rc;
+        if (int rc = pool_alloc(S->pool, 4ull * G->plans[i].k * S->viol_cap, sa, &vp, "violation buffer")) return rc;
         G->descs[i].viol = (int32_t*)vp;
         G->descs[i].viol_cap = S->viol_cap;
         S->used += (int64_t)(4ull * G->plans[i].k * S->viol_cap);
@@ -1079,13 +1111,19 @@ int session_admit(gfd_session* S) {
     }
     G->live = n;
     const bool refine = !(S->opts.flags & GFD_FLAG_NO_REFINE);
-    if (int rc = group_build(S->g, G.get(), S->T, refine, S->st)) return rc;
+    if (int rc = group_build(S->g, G.get(), S->T, refine, sa)) return rc;
     ProfEvents prof;
     int64_t launches[5] = {0, 0, 0, 0, 0};
-    const int lrc = group_launch(S->g, G.get(), S->T, S->pool, S->st, prof, launches);
+    const int lrc = group_launch(S->g, G.get(), S->T, S->pool, sa, prof, launches);
     S->used += (int64_t)G->cpi_bytes;
     if (lrc) return lrc;
-    return init_slots(enum_args(S->g, S->T), G->slot.data(), n, S->st);
+    // the session stream starts the new slots once their index is built (after
+    // whatever round it is running)
+    GFD_CUDA(cudaEventRecord(S->ev_admit, sa));
+    GFD_CUDA(cudaStreamWaitEvent(S->st, S->ev_admit, 0));
+    if (int rc = init_slots(enum_args(S->g, S->T), G->slot.data(), n, S->st)) return rc;
+    for (int i = 0; i < n; i++) S->slots[G->slot[i]].started = true;
+    return GFD_OK;
 }
 
 }  // namespace
@@ -1108,6 +1146,7 @@ void slot_release(gfd_session* S, SlotHost& sl) {
     sl.group.reset();
     sl.req.reset();
     sl.busy = false;
+    sl.started = false;
     sl.id = -1;
 }
 
@@ -1118,31 +1157,55 @@ int session_step(gfd_session* S, int32_t* n_advanced, int32_t* n_running, int32_
         set_error(GFD_ERR_INVALID_ARG, "gfd_session_step: NULL session");
         return GFD_ERR_INVALID_ARG;
     }
+    using clk = std::chrono::steady_clock;
+    // The round for the requests already running is launched first, its state
+    // snapshot copied to pinned memory behind it; queued requests are admitted
+    // meanwhile (planning on the host, index build on the admission stream), so
+    // admission overlaps the round; the new requests start after it.
+    std::vector<char> in_round(S->slots.size(), 0);
+    int busy = 0;  // requests in the round
+    auto launch_round = [&]() -> int {
+        busy = 0;
+        for (size_t i = 0; i < S->slots.size(); i++) {
+            in_round[i] = S->slots[i].busy && S->slots[i].started;
+            busy += in_round[i];
+        }
+        if (!busy) return GFD_OK;
+        GFD_CUDA(cudaGraphLaunch(S->exec, S->st));
+        GFD_CUDA(cudaMemcpyAsync(S->h_states, S->T.state, sizeof(SlotState) * S->slots.size(),
+                                 cudaMemcpyDeviceToHost, S->st));
+        GFD_CUDA(cudaMemcpyAsync(S->h_sched, S->T.sched, sizeof(Sched), cudaMemcpyDeviceToHost, S->st));
+        GFD_CUDA(cudaMemcpyAsync(S->h_err, S->T.err, sizeof(int32_t), cudaMemcpyDeviceToHost, S->st));
+        return GFD_OK;
+    };
+    const auto t0 = clk::now();
+    if (int rc = launch_round()) return rc;
+    const auto ta = clk::now();
     if (int rc = session_admit(S)) return rc;
-    int busy = 0;
-    for (auto& sl : S->slots) busy += sl.busy;
+    const auto t1 = clk::now();
+    S->stat[0] += std::chrono::duration<double, std::milli>(t1 - ta).count();
+    if (!busy)
+        if (int rc = launch_round()) return rc;  // nothing was running: run the admitted requests now
     if (n_advanced) *n_advanced = busy;
     if (busy) {
-        GFD_CUDA(cudaGraphLaunch(S->exec, S->st));
-        std::vector<SlotState> states(S->slots.size());
-        Sched hs{};
-        int32_t herr = 0;
-        GFD_CUDA(cudaMemcpyAsync(states.data(), S->T.state, sizeof(SlotState) * states.size(), cudaMemcpyDeviceToHost,
-                                 S->st));
-        GFD_CUDA(cudaMemcpyAsync(&hs, S->T.sched, sizeof(Sched), cudaMemcpyDeviceToHost, S->st));
-        GFD_CUDA(cudaMemcpyAsync(&herr, S->T.err, sizeof(int32_t), cudaMemcpyDeviceToHost, S->st));
         GFD_CUDA(cudaStreamSynchronize(S->st));
+        S->stat[1] += std::chrono::duration<double, std::milli>(clk::now() - t0).count() -
+                      std::chrono::duration<double, std::milli>(t1 - ta).count();
+        S->stat[2] += 1;
+        const SlotState* states = S->h_states;
+        const Sched& hs = *S->h_sched;
         if (hs.err == DERR_TIMEOUT) {
             set_error(GFD_ERR_TIMEOUT, "a device-side limit ran out in the serving session");
             return GFD_ERR_TIMEOUT;
         }
-        if (herr) {
+        if (*S->h_err) {
             set_error(GFD_ERR_OVERFLOW, "index capacity exceeded");
             return GFD_ERR_OVERFLOW;
         }
         for (size_t i = 0; i < S->slots.size(); i++) {
             SlotHost& sl = S->slots[i];
-            if (!sl.busy || states[i].cur >= 0) continue;
+            // slots started after the round's snapshot are not in it
+            if (!in_round[i] || !sl.busy || states[i].cur >= 0) continue;
             if (states[i].err) {
                 set_error(GFD_ERR_OVERFLOW, "request %lld: partial-match counter overflow", (long long)sl.id);
                 return GFD_ERR_OVERFLOW;
@@ -1201,6 +1264,10 @@ int session_cancel(gfd_session* S, int64_t id) {
         }
     set_error(GFD_ERR_INVALID_ARG, "gfd_session_cancel: no request %lld in the session", (long long)id);
     return GFD_ERR_INVALID_ARG;
+}
+
+double session_stat(const gfd_session* S, int32_t which) {
+    return S && which >= 0 && which < 5 ? S->stat[which] : 0.0;
 }
 
 int session_next_result(gfd_session* S, int64_t* id, gfd_result** out) {

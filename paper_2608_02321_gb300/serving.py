@@ -74,6 +74,7 @@ def serve(g: Graph, gfds, arrivals, max_slots: int = 64, budget_bytes: int = 40 
     t_end = time.perf_counter() - t0
     summary = _summary(arrivals, finish, matches, t_end)
     summary["peak_running"] = peak_running
+    summary["session"] = s.stats()
     return summary, results
 
 
