@@ -268,7 +268,9 @@ def main():
                     help="violation records stored per call before a re-run")
     ap.add_argument("--serve-rates", default="50,200,500,1000,2000",
                     help="Poisson arrival rates (req/s) of the serving leg; empty: skip")
-    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=3000,
+                    help="requests per arrival rate (at most --serve-seconds of arrivals)")
+    ap.add_argument("--serve-seconds", type=float, default=12.0)
     ap.add_argument("--n-gfds", type=int, default=0, help="validate only the first N GFDs (profiling)")
     ap.add_argument("--no-autotune", action="store_true", help="skip gfd_autotune before the warm-up")
     ap.add_argument("--kernel-variant", type=int, default=0, help="fixed enumeration kernel variant (1-6)")
@@ -407,7 +409,10 @@ def main():
                 "counters": cnt,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
-    # e2e: host GFDs in, sorted violation tuples back on the host
+    # e2e: host GFDs in, sorted violation tuples back on the host (one untimed
+    # warm-up call first: it allocates the pinned host block that later calls
+    # reuse)
+    G.violations_all(step())
     e2e_times = []
     d2h = 0
     for _ in range(max(1, min(3, args.steps))):
@@ -535,17 +540,20 @@ def main():
     if rates and args.workload == "batched":
         from synth import configs
         from paper_2608_02321_gb300 import serving as srv
-        reqs = configs.serving_requests(g, args.serve_requests)
-        serving = {"requests_per_rate": len(reqs), "max_slots": 64, "budget_gb": 40}
+        all_reqs = configs.serving_requests(g, args.serve_requests)
+        serving = {"max_slots": 64, "budget_gb": 40,
+                   "requests_per_rate": f"min({args.serve_requests}, rate x {args.serve_seconds:.0f} s)"}
         for lam in rates:
+            reqs = all_reqs[: max(1, min(len(all_reqs), int(lam * args.serve_seconds)))]
             arr = configs.poisson_arrivals(lam, len(reqs), seed=int(lam))
             torch.cuda.synchronize()
             cont, _ = srv.serve(dg, reqs, arr, max_slots=64, budget_bytes=40 << 30, stream=stream)
             torch.cuda.synchronize()
             ser = srv.serve_serial(dg, reqs, arr, stream=stream)
             serving[f"rate_{int(lam)}"] = {
+                "requests": len(reqs),
                 "continuous": {k: cont[k] for k in ("p50_ms", "p99_ms", "matches_per_s", "requests_per_s",
-                                                    "makespan_s", "peak_running")},
+                                                    "makespan_s", "peak_running", "session")},
                 "serial_plain": {k: ser[k] for k in ("p50_ms", "p99_ms", "matches_per_s", "requests_per_s",
                                                      "makespan_s")}}
 

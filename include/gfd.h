@@ -244,6 +244,11 @@ const int32_t *gfd_result_tuples(gfd_result *r);
  * result's buffer). Returns GFD_OK, GFD_ERR_INVALID_ARG (NULL or too small a
  * buffer), GFD_ERR_OUT_OF_MEMORY or a CUDA error code. */
 int gfd_result_copy_tuples(gfd_result *r, int32_t *out, uint64_t capacity);
+/* Copies of violation tuples into pageable host memory go through a page-locked
+ * double buffer of 2 x 64 MiB that the library allocates on first use and keeps
+ * until the process exits (host threads move each chunk into the destination
+ * while the next one crosses the link); page-locked destinations are copied
+ * directly. */
 /* The sorted tuples of n results (say, one gfd_validate_batch) written back to
  * back into caller-owned host memory `out` of `capacity` int32: result 0's
  * n_violations * k ints, then result 1's, and so on. One device sort over all of
@@ -322,9 +327,11 @@ int gfd_session_next_result(gfd_session *s, int64_t *request_id, gfd_result **ou
  * session holds no request with that id (unknown, or already collected). */
 int gfd_session_cancel(gfd_session *s, int64_t request_id);
 /* Session statistics since creation, for monitoring: 0 host milliseconds spent
- * admitting requests (planning, index builds), 1 milliseconds spent in
+ * admitting requests (planning, index builds), 1 device milliseconds of
  * enumeration rounds, 2 rounds run, 3 requests admitted, 4 admissions (groups
- * of requests admitted together). 0 for NULL or another `which`. */
+ * of requests admitted together). 0 for NULL or another `which`. While an
+ * admission keeps the host busy, gfd_session_step queues as many rounds as
+ * recent admissions took (running averages), so the device keeps working. */
 double gfd_session_stat(const gfd_session *s, int32_t which);
 /* Wait for the session's work, release it and any uncollected results. Free
  * every session of a graph before the graph: a session issues its work on the

@@ -229,9 +229,10 @@ class Result:
     def violations(self) -> np.ndarray:
         """[n_violations, k] int32, lexicographically sorted (sorted on the device)."""
         n, k = self.n_violations, self.k
+        if not n:
+            return np.empty((0, k), dtype=np.int32)
         out = np.empty((n, k), dtype=np.int32)
-        if n:
-            _check(_lib.gfd_result_copy_tuples(self._h, out.ctypes.data_as(C.c_void_p), C.c_uint64(n * k)))
+        _check(_lib.gfd_result_copy_tuples(self._h, out.ctypes.data_as(C.c_void_p), C.c_uint64(n * k)))
         return out
 
     def profile(self, which: int):

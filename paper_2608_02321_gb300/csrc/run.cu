@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <array>
 #include <chrono>
+#include <cmath>
 #include <cstdarg>
 #include <cstddef>
 #include <cstdio>
@@ -28,6 +29,8 @@
 #include <deque>
 #include <map>
 #include <memory>
+#include <mutex>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -945,6 +948,7 @@ struct gfd_session {
     cudaStream_t st = nullptr;        // enumeration rounds
     cudaStream_t st_admit = nullptr;  // index builds of admitted requests
     cudaEvent_t ev_admit = nullptr;   // an admission's index build is complete
+    cudaEvent_t ev_round[2] = {nullptr, nullptr};  // around the rounds of a step
     gfd::SlotState* h_states = nullptr;  // pinned snapshot after a round
     gfd::Sched* h_sched = nullptr;
     int32_t* h_err = nullptr;
@@ -963,6 +967,8 @@ struct gfd_session {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     double stat[5] = {0, 0, 0, 0, 0};  // gfd_session_stat
+    double admit_ms_avg = 0;  // running averages: one admission, one round
+    double round_ms_avg = 0;
 };
 
 namespace gfd {
@@ -981,8 +987,14 @@ int session_create(gfd_graph* g, int32_t max_slots, const gfd_opts* o, gfd_sessi
     S->budget = default_budget(g, o);
     S->viol_cap = o && o->max_violations_hint > 0 ? (uint64_t)o->max_violations_hint : (1ull << 20);
     S->slots.resize(max_slots);
-    GFD_CUDA(cudaStreamCreateWithFlags(&S->st_admit, cudaStreamNonBlocking));
+    // index builds run beside the enumeration rounds at the highest stream
+    // priority, so their blocks are scheduled as soon as the rounds free an SM
+    int prio_least = 0, prio_greatest = 0;
+    GFD_CUDA(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+    GFD_CUDA(cudaStreamCreateWithPriority(&S->st_admit, cudaStreamNonBlocking, prio_greatest));
     GFD_CUDA(cudaEventCreateWithFlags(&S->ev_admit, cudaEventDisableTiming));
+    GFD_CUDA(cudaEventCreate(&S->ev_round[0]));
+    GFD_CUDA(cudaEventCreate(&S->ev_round[1]));
     GFD_CUDA(cudaMallocHost((void**)&S->h_states, sizeof(SlotState) * max_slots));
     GFD_CUDA(cudaMallocHost((void**)&S->h_sched, sizeof(Sched)));
     GFD_CUDA(cudaMallocHost((void**)&S->h_err, sizeof(int32_t)));
@@ -1019,6 +1031,8 @@ void session_free(gfd_session* S) {
     if (S->h_sched) cudaFreeHost(S->h_sched);
     if (S->h_err) cudaFreeHost(S->h_err);
     if (S->ev_admit) cudaEventDestroy(S->ev_admit);
+    for (auto e : S->ev_round)
+        if (e) cudaEventDestroy(e);
     if (S->st_admit) cudaStreamDestroy(S->st_admit);
     cudaGetLastError();  // a failure here must not surface in a later, unrelated call
     delete S;
@@ -1164,6 +1178,13 @@ int session_step(gfd_session* S, int32_t* n_advanced, int32_t* n_running, int32_
     // admission overlaps the round; the new requests start after it.
     std::vector<char> in_round(S->slots.size(), 0);
     int busy = 0;  // requests in the round
+    // while an admission keeps the host busy, the GPU should not run dry: queue
+    // as many rounds as the last admissions took, by the running averages
+    const bool admitting = !S->queue.empty();
+    int rounds = 1;
+    if (admitting && S->round_ms_avg > 0)
+        rounds = (int)std::min(16.0, std::max(1.0, std::ceil(S->admit_ms_avg / S->round_ms_avg)));
+    int launched = 0;
     auto launch_round = [&]() -> int {
         busy = 0;
         for (size_t i = 0; i < S->slots.size(); i++) {
@@ -1171,7 +1192,10 @@ int session_step(gfd_session* S, int32_t* n_advanced, int32_t* n_running, int32_
             busy += in_round[i];
         }
         if (!busy) return GFD_OK;
-        GFD_CUDA(cudaGraphLaunch(S->exec, S->st));
+        GFD_CUDA(cudaEventRecord(S->ev_round[0], S->st));
+        for (int r = 0; r < rounds; r++) GFD_CUDA(cudaGraphLaunch(S->exec, S->st));
+        GFD_CUDA(cudaEventRecord(S->ev_round[1], S->st));
+        launched = rounds;
         GFD_CUDA(cudaMemcpyAsync(S->h_states, S->T.state, sizeof(SlotState) * S->slots.size(),
                                  cudaMemcpyDeviceToHost, S->st));
         GFD_CUDA(cudaMemcpyAsync(S->h_sched, S->T.sched, sizeof(Sched), cudaMemcpyDeviceToHost, S->st));
@@ -1181,17 +1205,31 @@ int session_step(gfd_session* S, int32_t* n_advanced, int32_t* n_running, int32_
     const auto t0 = clk::now();
     if (int rc = launch_round()) return rc;
     const auto ta = clk::now();
+    const int64_t admissions_before = (int64_t)S->stat[4];
     if (int rc = session_admit(S)) return rc;
     const auto t1 = clk::now();
-    S->stat[0] += std::chrono::duration<double, std::milli>(t1 - ta).count();
-    if (!busy)
+    const double admit_ms = std::chrono::duration<double, std::milli>(t1 - ta).count();
+    S->stat[0] += admit_ms;
+    if ((int64_t)S->stat[4] > admissions_before)
+        S->admit_ms_avg = S->admit_ms_avg > 0 ? 0.8 * S->admit_ms_avg + 0.2 * admit_ms : admit_ms;
+    if (!busy) {
+        rounds = 1;
         if (int rc = launch_round()) return rc;  // nothing was running: run the admitted requests now
+    }
     if (n_advanced) *n_advanced = busy;
     if (busy) {
         GFD_CUDA(cudaStreamSynchronize(S->st));
-        S->stat[1] += std::chrono::duration<double, std::milli>(clk::now() - t0).count() -
-                      std::chrono::duration<double, std::milli>(t1 - ta).count();
-        S->stat[2] += 1;
+        float gpu_ms = 0;  // the rounds' device time (they may overlap an admission)
+        if (cudaEventElapsedTime(&gpu_ms, S->ev_round[0], S->ev_round[1]) != cudaSuccess) {
+            cudaGetLastError();
+            gpu_ms = 0;
+        }
+        S->stat[1] += gpu_ms;
+        S->stat[2] += launched;
+        if (gpu_ms > 0) {
+            const double per = gpu_ms / launched;
+            S->round_ms_avg = S->round_ms_avg > 0 ? 0.8 * S->round_ms_avg + 0.2 * per : per;
+        }
         const SlotState* states = S->h_states;
         const Sched& hs = *S->h_sched;
         if (hs.err == DERR_TIMEOUT) {
@@ -1404,6 +1442,81 @@ __global__ void k_unpack_multi(const PackSrc* src, const int32_t* M, int W, cons
 
 }  // namespace
 
+// Device-to-host copy of results into caller memory, synchronous. A page-locked
+// destination takes one copy. A pageable one goes through a page-locked double
+// buffer of the library (allocated once, kept for the process) in chunks: while
+// a chunk crosses to the host, several host threads copy the previous one into
+// the destination, so the copy is not held to one thread's pageable-memory
+// bandwidth.
+namespace {
+
+constexpr size_t STAGE_CHUNK = 64ull << 20;
+constexpr int COPY_THREADS = 8;
+std::mutex g_stage_mu;
+void* g_stage[2] = {nullptr, nullptr};
+
+void par_memcpy(void* dst, const void* src, size_t n) {
+    if (n < (4u << 20)) {
+        memcpy(dst, src, n);
+        return;
+    }
+    const size_t per = ((n + COPY_THREADS - 1) / COPY_THREADS + 4095) & ~(size_t)4095;
+    std::vector<std::thread> th;
+    for (int t = 1; t < COPY_THREADS && (size_t)t * per < n; t++) {
+        const size_t a = (size_t)t * per, len = std::min(per, n - a);
+        th.emplace_back([=] { memcpy((char*)dst + a, (const char*)src + a, len); });
+    }
+    memcpy(dst, src, std::min(per, n));
+    for (auto& x : th) x.join();
+}
+
+}  // namespace
+
+int copy_to_host(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) return GFD_OK;
+    cudaPointerAttributes pa{};
+    const bool pinned = cudaPointerGetAttributes(&pa, dst) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+    std::unique_lock<std::mutex> lock(g_stage_mu);
+    if (!pinned && !g_stage[0]) {
+        if (cudaMallocHost(&g_stage[0], STAGE_CHUNK) != cudaSuccess ||
+            cudaMallocHost(&g_stage[1], STAGE_CHUNK) != cudaSuccess) {
+            cudaGetLastError();
+            if (g_stage[0]) cudaFreeHost(g_stage[0]);
+            g_stage[0] = g_stage[1] = nullptr;
+        }
+    }
+    if (pinned || !g_stage[0] || bytes <= (1u << 20)) {  // one copy
+        lock.unlock();
+        GFD_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st));
+        GFD_CUDA(cudaStreamSynchronize(st));
+        return GFD_OK;
+    }
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int rc = GFD_OK;
+    for (auto& e : ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) rc = GFD_ERR_CUDA;
+    const size_t nch = (bytes + STAGE_CHUNK - 1) / STAGE_CHUNK;
+    for (size_t c = 0; c <= nch && rc == GFD_OK; c++) {
+        if (c < nch) {  // chunk c into buffer c % 2 (its previous chunk was copied out in step c - 1)
+            const size_t off = c * STAGE_CHUNK, len = std::min(STAGE_CHUNK, bytes - off);
+            cudaError_t e = cudaMemcpyAsync(g_stage[c & 1], (const char*)src + off, len, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[c & 1], st);
+            if (e != cudaSuccess) rc = cuda_fail(e, "staged result copy");
+        }
+        if (c > 0 && rc == GFD_OK) {  // chunk c - 1 into the destination
+            const size_t off = (c - 1) * STAGE_CHUNK, len = std::min(STAGE_CHUNK, bytes - off);
+            cudaError_t e = cudaEventSynchronize(ev[(c - 1) & 1]);
+            if (e != cudaSuccess) rc = cuda_fail(e, "staged result copy");
+            else par_memcpy((char*)dst + off, g_stage[(c - 1) & 1], len);
+        }
+    }
+    if (rc != GFD_OK) cudaStreamSynchronize(st);  // no copy into the buffers may remain in flight
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    return rc;
+}
+
 // Lexicographic order of the violation tuples (Vio is a set; this fixes a
 // canonical order): least-significant-first stable radix sorts over pairs of
 // columns, carrying a permutation.
@@ -1458,9 +1571,7 @@ int result_sort_copy(gfd_result* r, int32_t* dst) {
     }
     if (rc == GFD_OK) {
         k_gather_rows<<<grid, 256, 0, st>>>(r->d_viol, k, pb.Current(), n, sorted);
-        cudaError_t e = cudaMemcpyAsync(dst, sorted, 4 * n * k, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) rc = cuda_fail(e, "violation copy");
+        rc = copy_to_host(dst, sorted, 4 * n * k, st);
     }
     cudaFreeAsync(tmp, st);
     cudaFreeAsync(p0, st);
@@ -1545,9 +1656,7 @@ int results_sort_copy(gfd_result* const* rs, int n, int32_t* out, uint64_t capac
     }
     if (rc == GFD_OK) {
         k_unpack_multi<<<grid, 256, 0, st>>>(d_src, M, W, pb.Current(), total, dout);
-        cudaError_t e = cudaMemcpyAsync(out, dout, 4 * ints, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) rc = cuda_fail(e, "violation copy");
+        rc = copy_to_host(out, dout, 4 * ints, st);
     }
     cudaFreeAsync(tmp, st);
     cudaFreeAsync(d_src, st);
