@@ -157,7 +157,7 @@ typedef struct {
 
 #define GFD_FLAG_COUNT         0x80 /* counting pass: run the enumeration with an
                                        instrumented kernel that counts what the
-                                       run reads (gfd_result_stat 7..24); the
+                                       run reads (gfd_result_stat 7..28); the
                                        results are unchanged, the run is slower */
 
 /* Tuning options; a NULL gfd_opts* or zero fields select the defaults. */
@@ -266,7 +266,7 @@ double gfd_result_profile(const gfd_result *r, int32_t which, int64_t *launches)
  * matches written, 3 edge-lookup probes (whole run), 4 candidate-list entries
  * (sum over pattern nodes), 5 index entries, 6 number of extra runs made
  * because the violations of the call outgrew max_violations_hint. With
- * GFD_FLAG_COUNT, 7..24 are the whole call's counters of what its kernels read:
+ * GFD_FLAG_COUNT, 7..28 are the whole call's counters of what its kernels read:
  * 7 work items (entries of the index lists N_u, Section III.B, or of another
  * candidate list), 8 of them at the last level, 9 partial matches expanded,
  * 10 sum over expanded partial matches of the adjacency lengths of their
@@ -277,7 +277,9 @@ double gfd_result_profile(const gfd_result *r, int32_t which, int64_t *launches)
  * loads, 18 attribute loads of literal checks, 19 partial matches written,
  * 20 candidates whose adjacency the refinement and index build scanned, 21
  * adjacency entries they read, 22 warp iterations of the expansion, 23 sum over
- * them of the largest number of search loads one lane made, 24 the number of
+ * them of the largest number of search loads one lane made, 24..26 SM cycles
+ * warps spent setting up tiles, in iterations at intermediate levels and at the
+ * last level, 27 warp iterations at intermediate levels, 28 the number of
  * distinct filter keys (high 32 bits) and of candidate bitmaps compacted (low
  * 32 bits). */
 uint64_t gfd_result_stat(const gfd_result *r, int32_t which);

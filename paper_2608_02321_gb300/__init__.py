@@ -39,10 +39,11 @@ FLAG_COUNT = 0x80
 
 PROF_FILTER, PROF_REFINE, PROF_INDEX, PROF_ENUM, PROF_SORT = range(5)
 STAT_STEPS, STAT_WORK, STAT_ROWS, STAT_PROBES, STAT_CANDIDATES, STAT_INDEX, STAT_RERUN = range(7)
-# counters of a GFD_FLAG_COUNT run (gfd_result_stat 7..24)
+# counters of a GFD_FLAG_COUNT run (gfd_result_stat 7..28)
 COUNTERS = ("items", "items_last", "partials", "back_deg", "checks", "sig_settled", "searches",
             "search_loads", "neg_checks", "neg_logd", "sig_loads", "attr_reads", "rows",
-            "scan_cands", "scan_entries", "iters", "iter_max_loads", "keys_and_bitmaps")
+            "scan_cands", "scan_entries", "iters", "iter_max_loads", "cyc_tile", "cyc_mid", "cyc_last",
+            "iters_mid", "keys_and_bitmaps")
 
 
 class GfdError(RuntimeError):

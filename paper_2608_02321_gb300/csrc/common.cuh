@@ -167,8 +167,12 @@ enum : int {
     CNT_ITERS,         // warp iterations of the expansion (32 work items each at most)
     CNT_ITER_MAX_LOADS,// sum over warp iterations of the largest number of search
                        // loads one lane made (the warp waits for its slowest lane)
+    CNT_CYC_TILE,      // SM cycles warps spent setting up tiles (row range searches)
+    CNT_CYC_MID,       // SM cycles of warp iterations at intermediate levels
+    CNT_CYC_LAST,      // SM cycles of warp iterations at the last level
+    CNT_ITERS_MID,     // warp iterations at intermediate levels
     CNT_HOST,          // filled by the host: distinct filter keys << 32 | bitmaps
-    N_CNT = 18
+    N_CNT = 22
 };
 
 // Scheduler state shared by all slots of a run (device).

@@ -55,7 +55,9 @@ template <bool COUNT>
 struct Counters {
     __device__ __forceinline__ void add(int, uint64_t) {}
     __device__ __forceinline__ uint32_t* loads() { return nullptr; }
-    __device__ __forceinline__ void iteration() {}
+    __device__ __forceinline__ void iteration(bool) {}
+    __device__ __forceinline__ void mark() {}
+    __device__ __forceinline__ void cycles(int) {}
     __device__ __forceinline__ void flush(Sched*) {}
 };
 template <>
@@ -64,15 +66,25 @@ struct Counters<true> {
     uint32_t search_loads = 0;  // of the current warp iteration
     __device__ __forceinline__ void add(int i, uint64_t v) { c[i] += v; }
     __device__ __forceinline__ uint32_t* loads() { return &search_loads; }
+    long long t0 = 0;  // clock at the start of the current phase
+    __device__ __forceinline__ void mark() { t0 = clock64(); }
+    // SM cycles since mark() into counter i (lane 0 counts for the warp)
+    __device__ __forceinline__ void cycles(int i) {
+        const long long t = clock64();
+        if ((threadIdx.x & 31) == 0) c[i] += (uint64_t)(t - t0);
+        t0 = t;
+    }
     // end of a warp iteration (all lanes): the slowest lane's search loads
-    __device__ __forceinline__ void iteration() {
+    __device__ __forceinline__ void iteration(bool last) {
         const uint32_t mx = __reduce_max_sync(0xffffffffu, search_loads);
         if ((threadIdx.x & 31) == 0) {
             c[CNT_ITERS] += 1;
             c[CNT_ITER_MAX_LOADS] += mx;
+            if (!last) c[CNT_ITERS_MID] += 1;
         }
         c[CNT_SEARCH_LOADS] += search_loads;
         search_loads = 0;
+        cycles(last ? CNT_CYC_LAST : CNT_CYC_MID);
     }
     __device__ void flush(Sched* s) {
         for (int i = 0; i < N_CNT; i++) {
@@ -252,6 +264,7 @@ __device__ void expand_warps(const EnumArgs& A) {
     const uint64_t tile = *(volatile uint32_t*)&A.sched->tile;  // work items per tile in this step
     uint64_t probes = 0;
     for (uint64_t t = gwarp; t < total_tiles;) {
+        cn.mark();
         const int s = (int)warp_find(A.tile_base, 0, (uint64_t)A.n_slots, t, lane);
         const SlotDesc* __restrict__ D = A.slots + s;
         SlotState* S = A.state + s;
@@ -291,6 +304,7 @@ __device__ void expand_warps(const EnumArgs& A) {
         }
         uint64_t tile_matches = 0;
         uint32_t cur = rlo;  // row of the first work item of the iteration
+        cn.cycles(CNT_CYC_TILE);
         for (uint64_t w0 = wb; w0 < we; w0 += 32) {
             const uint64_t w = w0 + lane;
             bool ok = w < we;
@@ -609,7 +623,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                     }
                 }
             }
-            cn.iteration();
+            cn.iteration(last);
         }
         if (last) {
             const unsigned long long tm = __reduce_add_sync(0xffffffffu, (unsigned)tile_matches);
