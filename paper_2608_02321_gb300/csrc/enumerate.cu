@@ -30,6 +30,7 @@
 #include <cub/cub.cuh>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "engine.h"
 
@@ -262,7 +263,7 @@ __device__ void expand_warps(const EnumArgs& A) {
     const DevGraph& g = A.g;
     const uint32_t total_tiles = *(volatile uint32_t*)&A.sched->total_tiles;
     const uint64_t tile = *(volatile uint32_t*)&A.sched->tile;  // work items per tile in this step
-    uint64_t probes = 0;
+    uint32_t probes = 0;  // a statistic (saturates per warp)
     for (uint64_t t = gwarp; t < total_tiles;) {
         cn.mark();
         const int s = (int)warp_find(A.tile_base, 0, (uint64_t)A.n_slots, t, lane);
@@ -302,339 +303,350 @@ __device__ void expand_warps(const EnumArgs& A) {
                 rhi1 = (uint32_t)nrows;
             }
         }
-        uint64_t tile_matches = 0;
-        uint32_t cur = rlo;  // row of the first work item of the iteration
-        cn.cycles(CNT_CYC_TILE);
-        for (uint64_t w0 = wb; w0 < we; w0 += 32) {
-            const uint64_t w = w0 + lane;
-            bool ok = w < we;
-            uint32_t v = 0;
-            int32_t j = 0;
-            const int32_t* rowp = nullptr;
-            uint32_t r = 0;
-            // Rows of this iteration's 32 work items: stored rows have fan-out
-            // >= 1, so they lie in the window [cur, cur + 32); one coalesced load
-            // of the window's prefixes and a 5-step shuffle search per lane. A
-            // lane left at the window's end checks the next prefix and falls
-            // back to a binary search (root candidates may have no fan-out).
-            uint64_t sr = 0;
-            if (list1) {
-                r = ok ? (uint32_t)(w / c1) : 0u;
-                sr = (uint64_t)r * c1;
-            } else if (k > 1) {
-                const uint64_t widx = (uint64_t)cur + lane;
-                const uint64_t sv = widx < rhi1 ? (l == 0 ? (uint64_t)__ldg(S0 + widx) : ld_front(Sl + widx))
-                                                : ~0ull;
-                int pos = 0;
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const uint64_t x = __shfl_sync(0xffffffffu, sv, pos + step);
-                    if (x <= w) pos += step;
-                }
-                sr = __shfl_sync(0xffffffffu, sv, pos);
-                r = cur + pos;
-                if (ok && pos == 31 && r + 1 < rhi1) {
-                    const uint64_t nxt = l == 0 ? (uint64_t)__ldg(S0 + r + 1) : ld_front(Sl + r + 1);
-                    if (nxt <= w) {
-                        r = l == 0 ? find_row_in(S0, r, rhi1, w) : find_row_in(Sl, r, rhi1, w);
-                        sr = l == 0 ? (uint64_t)__ldg(S0 + r) : ld_front(Sl + r);
+        // The tile's items, compiled twice: for the last level (literal check,
+        // violations) and for the others (fan-out, new partial matches), so
+        // that neither path carries the other's registers.
+        auto run_tile = [&](auto last_tag) {
+            constexpr bool LAST = decltype(last_tag)::value;
+            uint32_t tile_matches = 0;
+            uint32_t cur = rlo;  // row of the first work item of the iteration
+            cn.cycles(CNT_CYC_TILE);
+            for (uint64_t w0 = wb; w0 < we; w0 += 32) {
+                const uint64_t w = w0 + lane;
+                bool ok = w < we;
+                uint32_t v = 0;
+                int32_t j = 0;
+                const int32_t* rowp = nullptr;
+                uint32_t r = 0;
+                // Rows of this iteration's 32 work items: stored rows have fan-out
+                // >= 1, so they lie in the window [cur, cur + 32); one coalesced load
+                // of the window's prefixes and a 5-step shuffle search per lane. A
+                // lane left at the window's end checks the next prefix and falls
+                // back to a binary search (root candidates may have no fan-out).
+                uint64_t sr = 0;
+                if (list1) {
+                    r = ok ? (uint32_t)(w / c1) : 0u;
+                    sr = (uint64_t)r * c1;
+                } else if (k > 1) {
+                    const uint64_t widx = (uint64_t)cur + lane;
+                    const uint64_t sv = widx < rhi1 ? (l == 0 ? (uint64_t)__ldg(S0 + widx) : ld_front(Sl + widx))
+                                                    : ~0ull;
+                    int pos = 0;
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const uint64_t x = __shfl_sync(0xffffffffu, sv, pos + step);
+                        if (x <= w) pos += step;
                     }
-                }
-                cur = __shfl_sync(0xffffffffu, r, 31);
-            }
-            if (ok) {
-                cn.add(CNT_ITEMS, 1);
-                if (last) cn.add(CNT_ITEMS_LAST, 1);
-                if (k == 1) {
-                    j = (int32_t)w;
-                    v = (uint32_t)D->cand[0][j];
-                } else {
-                    const uint64_t o = w - sr;
-                    uint64_t ent;  // index of the candidate's index edge
-                    int choice = 0;
-                    if (l == 0) {
-                        // the roots' index edges are level 1's, in work-item order
-                        // (or level 1's candidate list when it starts a component)
-                        ent = list1 ? o : w;
-                        choice = list1 ? GEN_LIST : 0;
-                        m[0] = (uint32_t)D->cand[0][r];
-                    } else {
-                        // the row's ids in 16-byte loads (rows are padded to 16 B;
-                        // m has room for the last group), generator and index base
-                        // in one 8-byte load
-                        rowp = rows_l + (uint64_t)r * rw;
-                        const int4* r4 = reinterpret_cast<const int4*>(rowp);
-                        for (int q = 0; q <= l; q += 4) {
-                            const int4 t4 = r4[q >> 2];
-                            m[q << 5] = (uint32_t)t4.x;
-                            m[(q + 1) << 5] = (uint32_t)t4.y;
-                            m[(q + 2) << 5] = (uint32_t)t4.z;
-                            m[(q + 3) << 5] = (uint32_t)t4.w;
+                    sr = __shfl_sync(0xffffffffu, sv, pos);
+                    r = cur + pos;
+                    if (ok && pos == 31 && r + 1 < rhi1) {
+                        const uint64_t nxt = l == 0 ? (uint64_t)__ldg(S0 + r + 1) : ld_front(Sl + r + 1);
+                        if (nxt <= w) {
+                            r = l == 0 ? find_row_in(S0, r, rhi1, w) : find_row_in(Sl, r, rhi1, w);
+                            sr = l == 0 ? (uint64_t)__ldg(S0 + r) : ld_front(Sl + r);
                         }
-                        const int2 gb = *reinterpret_cast<const int2*>(rowp + 2 * (l + 1));
-                        choice = gb.x;
-                        ent = (uint64_t)(uint32_t)gb.y + o;
                     }
-                    int skip = -1;
-                    // the first pair check's earlier image is the same for all the
-                    // row's candidates: its signature half (the one that holds v
-                    // if the edge exists) is loaded while the candidate is fetched
-                    uint64_t sx0 = 0;
-                    if (nchk > 0) {
-                        const uint32_t w0c = cw[0];
-                        sx0 = sig_half(g, m[(w0c & 15u) << 5], (w0c >> 4) & 1u);
-                    }
-                    if (COUNT && o == 0) {
-                        // the row's first item: the partial match is expanded once;
-                        // a merge-based intersection would scan the adjacency of
-                        // each backward non-tree neighbour's image
-                        cn.add(CNT_PARTIALS, 1);
-                        uint64_t bd = 0;
-                        for (int c = 0; c < nchk; c++) {
-                            if (LP.chk_exp[c] == EXP_NONE) continue;
-                            const uint32_t x = m[LP.chk_q[c] << 5];
-                            bd += LP.chk_dir[c] ? g.in_off[x + 1] - g.in_off[x] : g.out_off[x + 1] - g.out_off[x];
-                        }
-                        cn.add(CNT_BACK_DEG, bd);
-                    }
-                    if (choice == 0) {
-                        // candidates from the index edges of the spanning-tree parent
-                        const int2 e = __ldg(D->cpi_idx[i] + ent);
-                        j = e.x;
-                        v = (uint32_t)e.y;
-                    } else if (GEN && choice == GEN_LIST) {
-                        // the level starts a component: its candidate list
-                        j = (int32_t)ent;
-                        v = (uint32_t)__ldg(D->cand[i] + ent);
+                    cur = __shfl_sync(0xffffffffu, r, 31);
+                }
+                if (ok) {
+                    cn.add(CNT_ITEMS, 1);
+                    if (LAST) cn.add(CNT_ITEMS_LAST, 1);
+                    if (k == 1) {
+                        j = (int32_t)w;
+                        v = (uint32_t)D->cand[0][j];
                     } else {
-                        // candidates from the adjacency of the other end of a
-                        // required back edge (the shorter list): keep those in
-                        // C(u) and probe the spanning-tree edge instead
-                        const int cg = LP.gen[choice - 1];
-                        skip = cg;
-                        const uint32_t x = m[LP.chk_q[cg] << 5];
-                        const uint32_t p = LP.chk_dir[cg] ? __ldg(g.in_adj + __ldg(g.in_off + x) + o)
-                                                          : __ldg(g.out_adj + __ldg(g.out_off + x) + o);
-                        v = p >> g.lbits;
-                        ok = exp_ok(LP.chk_exp[cg], (int32_t)(p & g.lmask)) &&
-                             ((__ldg(D->bm[i] + (v >> 5)) >> (v & 31)) & 1u);
-                        if (ok) {
-                            j = cand_rank(D->bm[i], D->rank[i], v);
-                            const uint32_t xp = m[LP.par << 5];
-                            // tree edge xp -> v (tdir 1) or v -> xp: the parent's
-                            // signature first, then v's
-                            bool maybe = (sig_half(g, xp, LP.tdir ? 0 : 1) >> sig_bit(v)) & 1ull;
-                            cn.add(CNT_SIG_LOADS, 1);
-                            if (maybe) {
-                                maybe = (sig_half(g, v, LP.tdir ? 1 : 0) >> sig_bit(xp)) & 1ull;
+                        // the item's offset within its row's candidates, and the
+                        // position of its index edge (both below 2^32: fan-outs and
+                        // index lists are 32-bit)
+                        const uint32_t o = (uint32_t)(w - sr);
+                        uint32_t ent;
+                        int choice = 0;
+                        if (l == 0) {
+                            // the roots' index edges are level 1's, in work-item order
+                            // (or level 1's candidate list when it starts a component)
+                            ent = list1 ? o : (uint32_t)w;
+                            choice = list1 ? GEN_LIST : 0;
+                            m[0] = (uint32_t)D->cand[0][r];
+                        } else {
+                            // the row's ids in 16-byte loads (rows are padded to 16 B;
+                            // m has room for the LAST group), generator and index base
+                            // in one 8-byte load
+                            rowp = rows_l + (uint64_t)r * rw;
+                            const int4* r4 = reinterpret_cast<const int4*>(rowp);
+                            for (int q = 0; q <= l; q += 4) {
+                                const int4 t4 = r4[q >> 2];
+                                m[q << 5] = (uint32_t)t4.x;
+                                m[(q + 1) << 5] = (uint32_t)t4.y;
+                                m[(q + 2) << 5] = (uint32_t)t4.z;
+                                m[(q + 3) << 5] = (uint32_t)t4.w;
+                            }
+                            const int2 gb = *reinterpret_cast<const int2*>(rowp + 2 * (l + 1));
+                            choice = gb.x;
+                            ent = (uint32_t)gb.y + o;
+                        }
+                        int skip = -1;
+                        // the first pair check's earlier image is the same for all the
+                        // row's candidates: its signature half (the one that holds v
+                        // if the edge exists) is loaded while the candidate is fetched
+                        uint64_t sx0 = 0;
+                        if (nchk > 0) {
+                            const uint32_t w0c = cw[0];
+                            sx0 = sig_half(g, m[(w0c & 15u) << 5], (w0c >> 4) & 1u);
+                        }
+                        if (COUNT && o == 0) {
+                            // the row's first item: the partial match is expanded once;
+                            // a merge-based intersection would scan the adjacency of
+                            // each backward non-tree neighbour's image
+                            cn.add(CNT_PARTIALS, 1);
+                            uint64_t bd = 0;
+                            for (int c = 0; c < nchk; c++) {
+                                if (LP.chk_exp[c] == EXP_NONE) continue;
+                                const uint32_t x = m[LP.chk_q[c] << 5];
+                                bd += LP.chk_dir[c] ? g.in_off[x + 1] - g.in_off[x] : g.out_off[x + 1] - g.out_off[x];
+                            }
+                            cn.add(CNT_BACK_DEG, bd);
+                        }
+                        if (choice == 0) {
+                            // candidates from the index edges of the spanning-tree parent
+                            const int2 e = __ldg(D->cpi_idx[i] + ent);
+                            j = e.x;
+                            v = (uint32_t)e.y;
+                        } else if (GEN && choice == GEN_LIST) {
+                            // the level starts a component: its candidate list
+                            j = (int32_t)ent;
+                            v = (uint32_t)__ldg(D->cand[i] + ent);
+                        } else {
+                            // candidates from the adjacency of the other end of a
+                            // required back edge (the shorter list): keep those in
+                            // C(u) and probe the spanning-tree edge instead
+                            const int cg = LP.gen[choice - 1];
+                            skip = cg;
+                            const uint32_t x = m[LP.chk_q[cg] << 5];
+                            const uint32_t p = LP.chk_dir[cg] ? __ldg(g.in_adj + __ldg(g.in_off + x) + o)
+                                                              : __ldg(g.out_adj + __ldg(g.out_off + x) + o);
+                            v = p >> g.lbits;
+                            ok = exp_ok(LP.chk_exp[cg], (int32_t)(p & g.lmask)) &&
+                                 ((__ldg(D->bm[i] + (v >> 5)) >> (v & 31)) & 1u);
+                            if (ok) {
+                                j = cand_rank(D->bm[i], D->rank[i], v);
+                                const uint32_t xp = m[LP.par << 5];
+                                // tree edge xp -> v (tdir 1) or v -> xp: the parent's
+                                // signature first, then v's
+                                bool maybe = (sig_half(g, xp, LP.tdir ? 0 : 1) >> sig_bit(v)) & 1ull;
                                 cn.add(CNT_SIG_LOADS, 1);
-                            }
-                            int32_t gl = NOEDGE;
-                            cn.add(CNT_CHECKS, 1);
-                            if (maybe) {
-                                cn.add(CNT_SEARCHES, 1);
-                                gl = LP.tdir ? edge_label(g, xp, g.out_off[xp], g.out_off[xp + 1], v, g.in_off[v], g.in_off[v + 1], cn.loads())
-                                             : edge_label(g, v, g.out_off[v], g.out_off[v + 1], xp, g.in_off[xp], g.in_off[xp + 1], cn.loads());
-                            } else {
-                                cn.add(CNT_SIG_SETTLED, 1);
-                            }
-                            probes++;
-                            ok = exp_ok(LP.tlab, gl);
-                        }
-                    }
-                    // injectivity
-                    for (int q = 0; q <= l && ok; q++)
-                        if (((LP.inj >> q) & 1u) && m[q << 5] == v) ok = false;
-                    // every other pattern pair, both directions (required edges
-                    // first): v's neighbourhood signatures settle most pairs (a
-                    // clear bit proves the edge absent); the rest search the
-                    // shorter adjacency list
-                    if (ok && nchk > 0) {
-                        const uint32_t bv = sig_bit(v);
-                        uint64_t svo = 0, svi = 0;  // v's signature, loaded when needed
-                        bool have_sv = false;
-                        for (int c = 0; c < nchk && ok; c++) {
-                            if (c == skip) continue;
-                            const uint32_t wd = cw[c];
-                            const uint32_t x = m[(wd & 15u) << 5];
-                            const bool out = (wd >> 4) & 1u;  // edge v -> x, else x -> v
-                            const int32_t ex = (int32_t)(int16_t)(wd >> 16);
-                            int32_t gl = NOEDGE;
-                            cn.add(CNT_CHECKS, 1);
-                            // v's bit in x's signature (x's in-neighbours for v -> x),
-                            // then x's bit in v's: a clear bit proves the edge absent
-                            const uint64_t sx = c == 0 ? sx0 : sig_half(g, x, out ? 1 : 0);
-                            if (c != 0) cn.add(CNT_SIG_LOADS, 1);
-                            bool maybe = (sx >> bv) & 1ull;
-                            if (maybe) {
-                                if (!have_sv) {
-                                    const ulonglong2 sg = __ldg(g.sig + v);
-                                    svo = sg.x;
-                                    svi = sg.y;
-                                    have_sv = true;
+                                if (maybe) {
+                                    maybe = (sig_half(g, v, LP.tdir ? 1 : 0) >> sig_bit(xp)) & 1ull;
                                     cn.add(CNT_SIG_LOADS, 1);
                                 }
-                                maybe = ((out ? svo : svi) >> sig_bit(x)) & 1ull;
-                            }
-                            if (COUNT && ex == EXP_NONE) {
-                                const uint32_t dv = out ? g.out_off[v + 1] - g.out_off[v] : g.in_off[v + 1] - g.in_off[v];
-                                const uint32_t dx = out ? g.in_off[x + 1] - g.in_off[x] : g.out_off[x + 1] - g.out_off[x];
-                                cn.add(CNT_NEG_CHECKS, 1);
-                                cn.add(CNT_NEG_LOGD, ceil_log2_1(min(dv, dx)));
-                            }
-                            if (maybe) {
-                                cn.add(CNT_SEARCHES, 1);
-                                gl = out ? edge_label(g, v, g.out_off[v], g.out_off[v + 1], x, g.in_off[x], g.in_off[x + 1],
-                                                      cn.loads())
-                                         : edge_label(g, x, g.out_off[x], g.out_off[x + 1], v, g.in_off[v], g.in_off[v + 1],
-                                                      cn.loads());
-                            } else {
-                                cn.add(CNT_SIG_SETTLED, 1);
-                            }
-                            probes++;
-                            ok = exp_ok(ex, gl);
-                        }
-                    }
-                }
-                m[i << 5] = v;
-                // X pushed down: the X literals whose ends are matched at this
-                // level (before the last one; the last level checks its own below)
-                if (GEN && ok && D->push_x && !last)
-                    for (int q = 0; q < D->nx && ok; q++)
-                        if (D->lit[q].lvl == i) ok = lit_holds(g, D->lit[q], m, COUNT ? &attr_reads : nullptr);
-            }
-            if (last) {
-                // complete match: check the X literals of this level, count it
-                // (with X pushed down only if they hold), check Y, emit a violation
-                bool viol = false;
-                if (ok) {
-                    bool x_ok = true;
-                    for (int q = 0; q < D->nx && x_ok; q++)
-                        if (!GEN || D->lit[q].lvl == i) x_ok = lit_holds(g, D->lit[q], m, COUNT ? &attr_reads : nullptr);
-                    if (GEN) tile_matches += x_ok || !D->push_x;
-                    else tile_matches++;
-                    if (x_ok) {
-                        bool y_ok = !D->y_false;
-                        for (int q = 0; q < D->ny && y_ok; q++)
-                            y_ok = lit_holds(g, D->lit[D->nx + q], m, COUNT ? &attr_reads : nullptr);
-                        viol = !y_ok;
-                    }
-                }
-                const uint32_t vb = __ballot_sync(0xffffffffu, viol);
-                if (vb) {
-                    unsigned long long base = 0;
-                    if (lane == 0) {
-                        const unsigned long long nv = __popc(vb);
-                        const unsigned long long old = atomicAdd((unsigned long long*)&S->n_viol, nv);
-                        base = D->viol ? old : atomicAdd((unsigned long long*)&A.sched->varena_used, nv);
-                    }
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    if (viol) {
-                        const uint64_t idx = base + __popc(vb & ((1u << lane) - 1u));
-                        if (D->viol) {
-                            // the slot's own buffer: tuples in pattern-node order
-                            if (idx < D->viol_cap) {
-                                int32_t* out = D->viol + idx * k;
-                                for (int q = 0; q < k; q++) out[D->order[q]] = (int32_t)m[q << 5];
-                            }
-                        } else if (idx < A.sched->varena_cap) {
-                            // the run's arena: [slot, tuple in pattern-node order]
-                            int32_t* rec = A.sched->varena + idx * A.sched->vstride;
-                            rec[0] = s;
-                            for (int q = 0; q < k; q++) rec[1 + D->order[q]] = (int32_t)m[q << 5];
-                        }
-                    }
-                }
-            } else {
-                // partial match of level i: append it with its fan-out for level
-                // i+1, taken from the shortest candidate generator (dead ends,
-                // with no fan-out, are dropped)
-                uint64_t fo = 0;
-                uint32_t nbase = 0;
-                int gen = 0;
-                if (ok) {
-                    const LevelPlan& L2 = D->lv[i + 1];
-                    const int pn = L2.par;
-                    if (GEN && pn < 0) {
-                        // level i+1 starts a component: its whole candidate list
-                        gen = GEN_LIST;
-                        fo = S->ncand[i + 1];
-                    } else {
-                        const uint32_t ppn = pn == i ? (uint32_t)j : (l == 0 ? r : (uint32_t)rowp[l + 1 + pn]);
-                        const uint32_t* co = D->cpi_off[i + 1];
-                        nbase = __ldg(co + ppn);
-                        fo = __ldg(co + ppn + 1) - nbase;
-                    }
-                    for (int q = 0; q < L2.ngen; q++) {
-                        const int cg = L2.gen[q];
-                        const uint32_t x = m[L2.chk_q[cg] << 5];
-                        const uint32_t d = L2.chk_dir[cg] ? __ldg(g.in_off + x + 1) - __ldg(g.in_off + x)
-                                                          : __ldg(g.out_off + x + 1) - __ldg(g.out_off + x);
-                        if (d < fo) {
-                            fo = d;
-                            gen = q + 1;
-                        }
-                    }
-                }
-                ok = ok && fo > 0;
-                const uint64_t packed = ok ? ((1ull << ROW_SHIFT) | fo) : 0ull;
-                uint64_t total;
-                const uint64_t excl = warp_excl_scan(packed, lane, &total);
-                if (total) {
-                    unsigned long long old = 0;
-                    if (lane == 0) {
-                        old = atomicAdd((unsigned long long*)&S->ctr[i], (unsigned long long)total);
-                        if ((old & WORK_MASK) + (total & WORK_MASK) > WORK_MASK ||
-                            (old >> ROW_SHIFT) + (total >> ROW_SHIFT) > D->chunk)
-                            atomicExch(&S->err, DERR_COUNTER_OVERFLOW);
-                    }
-                    old = __shfl_sync(0xffffffffu, old, 0);
-                    // the warp's new partial matches take rows [row0, row0 + its
-                    // count) of the level's buffer, in lane order
-                    if (ok) {
-                        const uint64_t row = (old >> ROW_SHIFT) + (excl >> ROW_SHIFT);
-                        if (row < D->chunk) {
-                            cn.add(CNT_ROWS, 1);
-                            // the row (ids, positions, generator, index base,
-                            // padding) in 16-byte stores, four ints at a time
-                            const int nw = row_width(i);
-                            int32_t* dst = D->rows[i] + row * nw;
-                            for (int t = 0; t < nw; t += 4) {
-                                int32_t e4[4];
-#pragma unroll
-                                for (int c = 0; c < 4; c++) {
-                                    const int idx = t + c;
-                                    int32_t val = 0;
-                                    if (idx <= i) {
-                                        val = (int32_t)m[idx << 5];
-                                    } else if (idx <= 2 * i + 1) {
-                                        const int q = idx - i - 1;
-                                        val = q == i ? j : (l == 0 ? (int32_t)r : rowp[l + 1 + q]);
-                                    } else if (idx == 2 * i + 2) {
-                                        val = gen;
-                                    } else if (idx == 2 * i + 3) {
-                                        val = (int32_t)nbase;
-                                    }
-                                    e4[c] = val;
+                                int32_t gl = NOEDGE;
+                                cn.add(CNT_CHECKS, 1);
+                                if (maybe) {
+                                    cn.add(CNT_SEARCHES, 1);
+                                    gl = LP.tdir ? edge_label(g, xp, g.out_off[xp], g.out_off[xp + 1], v, g.in_off[v], g.in_off[v + 1], cn.loads())
+                                                 : edge_label(g, v, g.out_off[v], g.out_off[v + 1], xp, g.in_off[xp], g.in_off[xp + 1], cn.loads());
+                                } else {
+                                    cn.add(CNT_SIG_SETTLED, 1);
                                 }
-                                *reinterpret_cast<int4*>(dst + t) = make_int4(e4[0], e4[1], e4[2], e4[3]);
+                                probes++;
+                                ok = exp_ok(LP.tlab, gl);
                             }
-                            D->wpre[i][row] = (old & WORK_MASK) + (excl & WORK_MASK);
+                        }
+                        // injectivity
+                        for (int q = 0; q <= l && ok; q++)
+                            if (((LP.inj >> q) & 1u) && m[q << 5] == v) ok = false;
+                        // every other pattern pair, both directions (required edges
+                        // first): v's neighbourhood signatures settle most pairs (a
+                        // clear bit proves the edge absent); the rest search the
+                        // shorter adjacency list
+                        if (ok && nchk > 0) {
+                            const uint32_t bv = sig_bit(v);
+                            uint64_t svo = 0, svi = 0;  // v's signature, loaded when needed
+                            bool have_sv = false;
+                            for (int c = 0; c < nchk && ok; c++) {
+                                if (c == skip) continue;
+                                const uint32_t wd = cw[c];
+                                const uint32_t x = m[(wd & 15u) << 5];
+                                const bool out = (wd >> 4) & 1u;  // edge v -> x, else x -> v
+                                const int32_t ex = (int32_t)(int16_t)(wd >> 16);
+                                int32_t gl = NOEDGE;
+                                cn.add(CNT_CHECKS, 1);
+                                // v's bit in x's signature (x's in-neighbours for v -> x),
+                                // then x's bit in v's: a clear bit proves the edge absent
+                                const uint64_t sx = c == 0 ? sx0 : sig_half(g, x, out ? 1 : 0);
+                                if (c != 0) cn.add(CNT_SIG_LOADS, 1);
+                                bool maybe = (sx >> bv) & 1ull;
+                                if (maybe) {
+                                    if (!have_sv) {
+                                        const ulonglong2 sg = __ldg(g.sig + v);
+                                        svo = sg.x;
+                                        svi = sg.y;
+                                        have_sv = true;
+                                        cn.add(CNT_SIG_LOADS, 1);
+                                    }
+                                    maybe = ((out ? svo : svi) >> sig_bit(x)) & 1ull;
+                                }
+                                if (COUNT && ex == EXP_NONE) {
+                                    const uint32_t dv = out ? g.out_off[v + 1] - g.out_off[v] : g.in_off[v + 1] - g.in_off[v];
+                                    const uint32_t dx = out ? g.in_off[x + 1] - g.in_off[x] : g.out_off[x + 1] - g.out_off[x];
+                                    cn.add(CNT_NEG_CHECKS, 1);
+                                    cn.add(CNT_NEG_LOGD, ceil_log2_1(min(dv, dx)));
+                                }
+                                if (maybe) {
+                                    cn.add(CNT_SEARCHES, 1);
+                                    gl = out ? edge_label(g, v, g.out_off[v], g.out_off[v + 1], x, g.in_off[x], g.in_off[x + 1],
+                                                          cn.loads())
+                                             : edge_label(g, x, g.out_off[x], g.out_off[x + 1], v, g.in_off[v], g.in_off[v + 1],
+                                                          cn.loads());
+                                } else {
+                                    cn.add(CNT_SIG_SETTLED, 1);
+                                }
+                                probes++;
+                                ok = exp_ok(ex, gl);
+                            }
+                        }
+                    }
+                    m[i << 5] = v;
+                    // X pushed down: the X literals whose ends are matched at this
+                    // level (before the LAST one; the LAST level checks its own below)
+                    if (GEN && ok && D->push_x && !LAST)
+                        for (int q = 0; q < D->nx && ok; q++)
+                            if (D->lit[q].lvl == i) ok = lit_holds(g, D->lit[q], m, COUNT ? &attr_reads : nullptr);
+                }
+                if (LAST) {
+                    // complete match: check the X literals of this level, count it
+                    // (with X pushed down only if they hold), check Y, emit a violation
+                    bool viol = false;
+                    if (ok) {
+                        bool x_ok = true;
+                        for (int q = 0; q < D->nx && x_ok; q++)
+                            if (!GEN || D->lit[q].lvl == i) x_ok = lit_holds(g, D->lit[q], m, COUNT ? &attr_reads : nullptr);
+                        if (GEN) tile_matches += x_ok || !D->push_x;
+                        else tile_matches++;
+                        if (x_ok) {
+                            bool y_ok = !D->y_false;
+                            for (int q = 0; q < D->ny && y_ok; q++)
+                                y_ok = lit_holds(g, D->lit[D->nx + q], m, COUNT ? &attr_reads : nullptr);
+                            viol = !y_ok;
+                        }
+                    }
+                    const uint32_t vb = __ballot_sync(0xffffffffu, viol);
+                    if (vb) {
+                        unsigned long long base = 0;
+                        if (lane == 0) {
+                            const unsigned long long nv = __popc(vb);
+                            const unsigned long long old = atomicAdd((unsigned long long*)&S->n_viol, nv);
+                            base = D->viol ? old : atomicAdd((unsigned long long*)&A.sched->varena_used, nv);
+                        }
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (viol) {
+                            const uint64_t idx = base + __popc(vb & ((1u << lane) - 1u));
+                            if (D->viol) {
+                                // the slot's own buffer: tuples in pattern-node order
+                                if (idx < D->viol_cap) {
+                                    int32_t* out = D->viol + idx * k;
+                                    for (int q = 0; q < k; q++) out[D->order[q]] = (int32_t)m[q << 5];
+                                }
+                            } else if (idx < A.sched->varena_cap) {
+                                // the run's arena: [slot, tuple in pattern-node order]
+                                int32_t* rec = A.sched->varena + idx * A.sched->vstride;
+                                rec[0] = s;
+                                for (int q = 0; q < k; q++) rec[1 + D->order[q]] = (int32_t)m[q << 5];
+                            }
+                        }
+                    }
+                } else {
+                    // partial match of level i: append it with its fan-out for level
+                    // i+1, taken from the shortest candidate generator (dead ends,
+                    // with no fan-out, are dropped)
+                    uint64_t fo = 0;
+                    uint32_t nbase = 0;
+                    int gen = 0;
+                    if (ok) {
+                        const LevelPlan& L2 = D->lv[i + 1];
+                        const int pn = L2.par;
+                        if (GEN && pn < 0) {
+                            // level i+1 starts a component: its whole candidate list
+                            gen = GEN_LIST;
+                            fo = S->ncand[i + 1];
+                        } else {
+                            const uint32_t ppn = pn == i ? (uint32_t)j : (l == 0 ? r : (uint32_t)rowp[l + 1 + pn]);
+                            const uint32_t* co = D->cpi_off[i + 1];
+                            nbase = __ldg(co + ppn);
+                            fo = __ldg(co + ppn + 1) - nbase;
+                        }
+                        for (int q = 0; q < L2.ngen; q++) {
+                            const int cg = L2.gen[q];
+                            const uint32_t x = m[L2.chk_q[cg] << 5];
+                            const uint32_t d = L2.chk_dir[cg] ? __ldg(g.in_off + x + 1) - __ldg(g.in_off + x)
+                                                              : __ldg(g.out_off + x + 1) - __ldg(g.out_off + x);
+                            if (d < fo) {
+                                fo = d;
+                                gen = q + 1;
+                            }
+                        }
+                    }
+                    ok = ok && fo > 0;
+                    const uint64_t packed = ok ? ((1ull << ROW_SHIFT) | fo) : 0ull;
+                    uint64_t total;
+                    const uint64_t excl = warp_excl_scan(packed, lane, &total);
+                    if (total) {
+                        unsigned long long old = 0;
+                        if (lane == 0) {
+                            old = atomicAdd((unsigned long long*)&S->ctr[i], (unsigned long long)total);
+                            if ((old & WORK_MASK) + (total & WORK_MASK) > WORK_MASK ||
+                                (old >> ROW_SHIFT) + (total >> ROW_SHIFT) > D->chunk)
+                                atomicExch(&S->err, DERR_COUNTER_OVERFLOW);
+                        }
+                        old = __shfl_sync(0xffffffffu, old, 0);
+                        // the warp's new partial matches take rows [row0, row0 + its
+                        // count) of the level's buffer, in lane order
+                        if (ok) {
+                            const uint64_t row = (old >> ROW_SHIFT) + (excl >> ROW_SHIFT);
+                            if (row < D->chunk) {
+                                cn.add(CNT_ROWS, 1);
+                                // the row (ids, positions, generator, index base,
+                                // padding) in 16-byte stores, four ints at a time
+                                const int nw = row_width(i);
+                                int32_t* dst = D->rows[i] + row * nw;
+                                for (int t = 0; t < nw; t += 4) {
+                                    int32_t e4[4];
+    #pragma unroll
+                                    for (int c = 0; c < 4; c++) {
+                                        const int idx = t + c;
+                                        int32_t val = 0;
+                                        if (idx <= i) {
+                                            val = (int32_t)m[idx << 5];
+                                        } else if (idx <= 2 * i + 1) {
+                                            const int q = idx - i - 1;
+                                            val = q == i ? j : (l == 0 ? (int32_t)r : rowp[l + 1 + q]);
+                                        } else if (idx == 2 * i + 2) {
+                                            val = gen;
+                                        } else if (idx == 2 * i + 3) {
+                                            val = (int32_t)nbase;
+                                        }
+                                        e4[c] = val;
+                                    }
+                                    *reinterpret_cast<int4*>(dst + t) = make_int4(e4[0], e4[1], e4[2], e4[3]);
+                                }
+                                D->wpre[i][row] = (old & WORK_MASK) + (excl & WORK_MASK);
+                            }
                         }
                     }
                 }
+                cn.iteration(LAST);
             }
-            cn.iteration(last);
-        }
-        if (last) {
-            const unsigned long long tm = __reduce_add_sync(0xffffffffu, (unsigned)tile_matches);
-            if (lane == 0 && tm) atomicAdd((unsigned long long*)&S->n_matches, tm);
-        }
+            if (LAST) {
+                const unsigned long long tm = __reduce_add_sync(0xffffffffu, tile_matches);
+                if (lane == 0 && tm) atomicAdd((unsigned long long*)&S->n_matches, tm);
+            }
+        };
+        if (last) run_tile(std::true_type{});
+        else run_tile(std::false_type{});
         uint32_t nt = 0;
         if (lane == 0) nt = atomicAdd(&A.sched->tile_next, 1u);
         t = nwarps + __shfl_sync(0xffffffffu, nt, 0);
     }
     // probe statistics: one atomic per warp
-    const unsigned long long p = __reduce_add_sync(0xffffffffu, (unsigned)min(probes, (uint64_t)0xffffffffu));
+    const unsigned long long p = __reduce_add_sync(0xffffffffu, probes);
     if (lane == 0 && p) atomicAdd((unsigned long long*)&A.sched->probes, p);
     if (COUNT) {
         cn.add(CNT_ATTR_READS, attr_reads);
