@@ -303,11 +303,14 @@ __device__ void expand_warps(const EnumArgs& A) {
                 rhi1 = (uint32_t)nrows;
             }
         }
-        // The tile's items, compiled twice: for the last level (literal check,
-        // violations) and for the others (fan-out, new partial matches), so
-        // that neither path carries the other's registers.
-        auto run_tile = [&](auto last_tag) {
+        // The tile's items, compiled for the last level (literal check,
+        // violations) and for the others (fan-out, new partial matches), each
+        // for the roots (level 0: candidate list, 32-bit index offsets) and for
+        // stored partial matches (rows, 64-bit prefixes), so that no path
+        // carries another's registers.
+        auto run_tile = [&](auto last_tag, auto root_tag) {
             constexpr bool LAST = decltype(last_tag)::value;
+            constexpr bool ROOT = decltype(root_tag)::value;  // expanding the roots (ROOT)
             uint32_t tile_matches = 0;
             uint32_t cur = rlo;  // row of the first work item of the iteration
             cn.cycles(CNT_CYC_TILE);
@@ -329,7 +332,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                     sr = (uint64_t)r * c1;
                 } else if (k > 1) {
                     const uint64_t widx = (uint64_t)cur + lane;
-                    const uint64_t sv = widx < rhi1 ? (l == 0 ? (uint64_t)__ldg(S0 + widx) : ld_front(Sl + widx))
+                    const uint64_t sv = widx < rhi1 ? (ROOT ? (uint64_t)__ldg(S0 + widx) : ld_front(Sl + widx))
                                                     : ~0ull;
                     int pos = 0;
                     for (int step = 16; step >= 1; step >>= 1) {
@@ -339,10 +342,10 @@ __device__ void expand_warps(const EnumArgs& A) {
                     sr = __shfl_sync(0xffffffffu, sv, pos);
                     r = cur + pos;
                     if (ok && pos == 31 && r + 1 < rhi1) {
-                        const uint64_t nxt = l == 0 ? (uint64_t)__ldg(S0 + r + 1) : ld_front(Sl + r + 1);
+                        const uint64_t nxt = ROOT ? (uint64_t)__ldg(S0 + r + 1) : ld_front(Sl + r + 1);
                         if (nxt <= w) {
-                            r = l == 0 ? find_row_in(S0, r, rhi1, w) : find_row_in(Sl, r, rhi1, w);
-                            sr = l == 0 ? (uint64_t)__ldg(S0 + r) : ld_front(Sl + r);
+                            r = ROOT ? find_row_in(S0, r, rhi1, w) : find_row_in(Sl, r, rhi1, w);
+                            sr = ROOT ? (uint64_t)__ldg(S0 + r) : ld_front(Sl + r);
                         }
                     }
                     cur = __shfl_sync(0xffffffffu, r, 31);
@@ -360,7 +363,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                         const uint32_t o = (uint32_t)(w - sr);
                         uint32_t ent;
                         int choice = 0;
-                        if (l == 0) {
+                        if (ROOT) {
                             // the roots' index edges are level 1's, in work-item order
                             // (or level 1's candidate list when it starts a component)
                             ent = list1 ? o : (uint32_t)w;
@@ -568,7 +571,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                             gen = GEN_LIST;
                             fo = S->ncand[i + 1];
                         } else {
-                            const uint32_t ppn = pn == i ? (uint32_t)j : (l == 0 ? r : (uint32_t)rowp[l + 1 + pn]);
+                            const uint32_t ppn = pn == i ? (uint32_t)j : (ROOT ? r : (uint32_t)rowp[l + 1 + pn]);
                             const uint32_t* co = D->cpi_off[i + 1];
                             nbase = __ldg(co + ppn);
                             fo = __ldg(co + ppn + 1) - nbase;
@@ -617,7 +620,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                                             val = (int32_t)m[idx << 5];
                                         } else if (idx <= 2 * i + 1) {
                                             const int q = idx - i - 1;
-                                            val = q == i ? j : (l == 0 ? (int32_t)r : rowp[l + 1 + q]);
+                                            val = q == i ? j : (ROOT ? (int32_t)r : rowp[l + 1 + q]);
                                         } else if (idx == 2 * i + 2) {
                                             val = gen;
                                         } else if (idx == 2 * i + 3) {
@@ -639,8 +642,13 @@ __device__ void expand_warps(const EnumArgs& A) {
                 if (lane == 0 && tm) atomicAdd((unsigned long long*)&S->n_matches, tm);
             }
         };
-        if (last) run_tile(std::true_type{});
-        else run_tile(std::false_type{});
+        if (last) {
+            if (l == 0) run_tile(std::true_type{}, std::true_type{});
+            else run_tile(std::true_type{}, std::false_type{});
+        } else {
+            if (l == 0) run_tile(std::false_type{}, std::true_type{});
+            else run_tile(std::false_type{}, std::false_type{});
+        }
         uint32_t nt = 0;
         if (lane == 0) nt = atomicAdd(&A.sched->tile_next, 1u);
         t = nwarps + __shfl_sync(0xffffffffu, nt, 0);
