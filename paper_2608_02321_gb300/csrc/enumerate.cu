@@ -145,6 +145,28 @@ __device__ __forceinline__ bool lit_holds(const DevGraph& g, const DevLit& L, co
     return vb != GFD_ATTR_ABSENT && va == vb;
 }
 
+// The same with the vertex of level lv given in a register (v) instead of the
+// shared-memory column (used when another lane's column holds the earlier
+// levels).
+__device__ __forceinline__ uint32_t level_vertex(const uint32_t* m, int q, int lv, uint32_t v) {
+    return q == lv ? v : m[q << 5];
+}
+__device__ __forceinline__ bool lit_holds_at(const DevGraph& g, const DevLit& L, const uint32_t* m, int lv, uint32_t v,
+                                             uint32_t* reads = nullptr) {
+    if (reads) ++*reads;
+    const int32_t va = __ldg(g.attrs + (uint64_t)L.a * g.n + level_vertex(m, L.xl, lv, v));
+    if (va == GFD_ATTR_ABSENT) return false;
+    if (L.kind == 0) return va == L.c;
+    if (reads) ++*reads;
+    const int32_t vb = __ldg(g.attrs + (uint64_t)L.b * g.n + level_vertex(m, L.yl, lv, v));
+    return vb != GFD_ATTR_ABSENT && va == vb;
+}
+
+// Partial matches of the second-to-last level with at most this many
+// candidates at the last level are expanded by the warp that makes them,
+// without being stored.
+constexpr uint32_t FUSE_FANOUT = 64;
+
 // Largest r in [0, n) with S[r] <= w (S non-decreasing, S[0] <= w). The index
 // offsets are read-only during enumeration; the frontier prefix is rewritten
 // between steps, so it is read through L2 only (ld.global.cg).
@@ -253,11 +275,13 @@ __device__ void expand_warps(const EnumArgs& A) {
     // banks) and the current tile's pair checks, packed.
     __shared__ uint32_t s_m[NT / 32][MAXK * 32];
     __shared__ uint32_t s_chk[NT / 32][2 * MAXK];
+    __shared__ uint32_t s_chk2[NT / 32][2 * MAXK];  // the last level's, for fused expansion
     Counters<COUNT> cn;
     uint32_t attr_reads = 0;
     const int lane = threadIdx.x & 31;
     uint32_t* const m = &s_m[threadIdx.x >> 5][lane];
     uint32_t* const cw = s_chk[threadIdx.x >> 5];
+    uint32_t* const cw2 = s_chk2[threadIdx.x >> 5];
     const uint64_t gwarp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const DevGraph& g = A.g;
@@ -313,6 +337,15 @@ __device__ void expand_warps(const EnumArgs& A) {
             constexpr bool ROOT = decltype(root_tag)::value;  // expanding the roots (ROOT)
             uint32_t tile_matches = 0;
             uint32_t cur = rlo;  // row of the first work item of the iteration
+            // a tile that makes partial matches of the second-to-last level
+            // expands the last level of those with small fan-outs at once
+            // (fused); the last level's pair checks are staged too
+            const bool fuse = !LAST && k >= 3 && i == k - 2;
+            if (fuse) {
+                __syncwarp();
+                if (lane < D->lv[k - 1].nchk) cw2[lane] = D->lv[k - 1].chk_w[lane];
+                __syncwarp();
+            }
             cn.cycles(CNT_CYC_TILE);
             for (uint64_t w0 = wb; w0 < we; w0 += 32) {
                 const uint64_t w = w0 + lane;
@@ -588,7 +621,9 @@ __device__ void expand_warps(const EnumArgs& A) {
                         }
                     }
                     ok = ok && fo > 0;
-                    const uint64_t packed = ok ? ((1ull << ROW_SHIFT) | fo) : 0ull;
+                    const bool fuse_me = fuse && ok && fo <= FUSE_FANOUT;  // expanded below, not stored
+                    const bool row_me = ok && !fuse_me;
+                    const uint64_t packed = row_me ? ((1ull << ROW_SHIFT) | fo) : 0ull;
                     uint64_t total;
                     const uint64_t excl = warp_excl_scan(packed, lane, &total);
                     if (total) {
@@ -602,7 +637,7 @@ __device__ void expand_warps(const EnumArgs& A) {
                         old = __shfl_sync(0xffffffffu, old, 0);
                         // the warp's new partial matches take rows [row0, row0 + its
                         // count) of the level's buffer, in lane order
-                        if (ok) {
+                        if (row_me) {
                             const uint64_t row = (old >> ROW_SHIFT) + (excl >> ROW_SHIFT);
                             if (row < D->chunk) {
                                 cn.add(CNT_ROWS, 1);
@@ -634,10 +669,170 @@ __device__ void expand_warps(const EnumArgs& A) {
                             }
                         }
                     }
+                    if (fuse) {
+                        // The last level of the lanes' new partial matches with small
+                        // fan-outs, by the whole warp, 32 items at a time: item t
+                        // belongs to the lane whose [fex, fex + ffo) holds t; that
+                        // lane's shared-memory column holds the partial match.
+                        const uint32_t ffo = fuse_me ? (uint32_t)fo : 0u;
+                        uint32_t fin = ffo;
+                        for (int d = 1; d < 32; d <<= 1) {
+                            const uint32_t y = __shfl_up_sync(0xffffffffu, fin, d);
+                            if (lane >= d) fin += y;
+                        }
+                        const uint32_t fex = fin - ffo;
+                        const uint32_t ftot = __shfl_sync(0xffffffffu, fin, 31);
+                        if (lane == 0 && ftot) atomicAdd((unsigned long long*)&S->st_work, (unsigned long long)ftot);
+                        __syncwarp();  // the lanes' columns, written above, are read by other lanes
+                        const int L = k - 1;
+                        const LevelPlan& LQ = D->lv[L];
+                        const int nchk2 = LQ.nchk;
+                        for (uint32_t fb = 0; fb < ftot; fb += 32) {
+                            const uint32_t it = fb + lane;
+                            int own = 0;
+                            for (int st = 16; st >= 1; st >>= 1) {
+                                const uint32_t x = __shfl_sync(0xffffffffu, fex, own + st);
+                                if (x <= it) own += st;
+                            }
+                            const uint32_t fo2 = it - __shfl_sync(0xffffffffu, fex, own);
+                            const uint32_t onb = __shfl_sync(0xffffffffu, nbase, own);
+                            const int och = __shfl_sync(0xffffffffu, gen, own);
+                            const uint32_t* mo = &s_m[threadIdx.x >> 5][own];
+                            bool iok = it < ftot;
+                            uint32_t fv = 0;
+                            int fskip = -1;
+                            if (iok) {
+                                cn.add(CNT_ITEMS, 1);
+                                cn.add(CNT_ITEMS_LAST, 1);
+                                if (COUNT && fo2 == 0) {
+                                    cn.add(CNT_PARTIALS, 1);
+                                    uint64_t bd = 0;
+                                    for (int c = 0; c < nchk2; c++) {
+                                        if (LQ.chk_exp[c] == EXP_NONE) continue;
+                                        const uint32_t x = mo[LQ.chk_q[c] << 5];
+                                        bd += LQ.chk_dir[c] ? g.in_off[x + 1] - g.in_off[x] : g.out_off[x + 1] - g.out_off[x];
+                                    }
+                                    cn.add(CNT_BACK_DEG, bd);
+                                }
+                                if (och == 0) {
+                                    fv = (uint32_t)__ldg(D->cpi_idx[L] + onb + fo2).y;
+                                } else if (GEN && och == GEN_LIST) {
+                                    fv = (uint32_t)__ldg(D->cand[L] + fo2);
+                                } else {
+                                    // from the adjacency of the other end of a required back
+                                    // edge: keep those in C(u) and probe the tree edge
+                                    const int cg = LQ.gen[och - 1];
+                                    fskip = cg;
+                                    const uint32_t x = mo[LQ.chk_q[cg] << 5];
+                                    const uint32_t pe = LQ.chk_dir[cg] ? __ldg(g.in_adj + __ldg(g.in_off + x) + fo2)
+                                                                       : __ldg(g.out_adj + __ldg(g.out_off + x) + fo2);
+                                    fv = pe >> g.lbits;
+                                    iok = exp_ok(LQ.chk_exp[cg], (int32_t)(pe & g.lmask)) &&
+                                          ((__ldg(D->bm[L] + (fv >> 5)) >> (fv & 31)) & 1u);
+                                    if (iok) {
+                                        const uint32_t xp = mo[LQ.par << 5];
+                                        bool maybe = (sig_half(g, xp, LQ.tdir ? 0 : 1) >> sig_bit(fv)) & 1ull;
+                                        if (maybe) maybe = (sig_half(g, fv, LQ.tdir ? 1 : 0) >> sig_bit(xp)) & 1ull;
+                                        int32_t gl = NOEDGE;
+                                        cn.add(CNT_CHECKS, 1);
+                                        if (maybe) {
+                                            cn.add(CNT_SEARCHES, 1);
+                                            gl = LQ.tdir ? edge_label(g, xp, g.out_off[xp], g.out_off[xp + 1], fv, g.in_off[fv],
+                                                                      g.in_off[fv + 1], cn.loads())
+                                                         : edge_label(g, fv, g.out_off[fv], g.out_off[fv + 1], xp, g.in_off[xp],
+                                                                      g.in_off[xp + 1], cn.loads());
+                                        } else {
+                                            cn.add(CNT_SIG_SETTLED, 1);
+                                        }
+                                        probes++;
+                                        iok = exp_ok(LQ.tlab, gl);
+                                    }
+                                }
+                                // injectivity, then the other pattern pairs
+                                for (int q = 0; q < L && iok; q++)
+                                    if (((LQ.inj >> q) & 1u) && mo[q << 5] == fv) iok = false;
+                                if (iok && nchk2 > 0) {
+                                    const uint32_t bv = sig_bit(fv);
+                                    uint64_t svo = 0, svi = 0;
+                                    bool have_sv = false;
+                                    for (int c = 0; c < nchk2 && iok; c++) {
+                                        if (c == fskip) continue;
+                                        const uint32_t wd = cw2[c];
+                                        const uint32_t x = mo[(wd & 15u) << 5];
+                                        const bool out = (wd >> 4) & 1u;
+                                        const int32_t ex = (int32_t)(int16_t)(wd >> 16);
+                                        cn.add(CNT_CHECKS, 1);
+                                        cn.add(CNT_SIG_LOADS, 1);
+                                        bool maybe = (sig_half(g, x, out ? 1 : 0) >> bv) & 1ull;
+                                        if (maybe) {
+                                            if (!have_sv) {
+                                                const ulonglong2 sg = __ldg(g.sig + fv);
+                                                svo = sg.x;
+                                                svi = sg.y;
+                                                have_sv = true;
+                                            }
+                                            maybe = ((out ? svo : svi) >> sig_bit(x)) & 1ull;
+                                        }
+                                        int32_t gl = NOEDGE;
+                                        if (maybe) {
+                                            cn.add(CNT_SEARCHES, 1);
+                                            gl = out ? edge_label(g, fv, g.out_off[fv], g.out_off[fv + 1], x, g.in_off[x],
+                                                                  g.in_off[x + 1], cn.loads())
+                                                     : edge_label(g, x, g.out_off[x], g.out_off[x + 1], fv, g.in_off[fv],
+                                                                  g.in_off[fv + 1], cn.loads());
+                                        } else {
+                                            cn.add(CNT_SIG_SETTLED, 1);
+                                        }
+                                        probes++;
+                                        iok = exp_ok(ex, gl);
+                                    }
+                                }
+                            }
+                            // complete match: X, count, Y, emit (as at the last level)
+                            bool fviol = false;
+                            if (iok) {
+                                bool x_ok = true;
+                                for (int q = 0; q < D->nx && x_ok; q++)
+                                    if (!GEN || D->lit[q].lvl == L)
+                                        x_ok = lit_holds_at(g, D->lit[q], mo, L, fv, COUNT ? &attr_reads : nullptr);
+                                if (GEN) tile_matches += x_ok || !D->push_x;
+                                else tile_matches++;
+                                if (x_ok) {
+                                    bool y_ok = !D->y_false;
+                                    for (int q = 0; q < D->ny && y_ok; q++)
+                                        y_ok = lit_holds_at(g, D->lit[D->nx + q], mo, L, fv, COUNT ? &attr_reads : nullptr);
+                                    fviol = !y_ok;
+                                }
+                            }
+                            const uint32_t vb = __ballot_sync(0xffffffffu, fviol);
+                            if (vb) {
+                                unsigned long long base = 0;
+                                if (lane == 0) {
+                                    const unsigned long long nv = __popc(vb);
+                                    const unsigned long long oldv = atomicAdd((unsigned long long*)&S->n_viol, nv);
+                                    base = D->viol ? oldv : atomicAdd((unsigned long long*)&A.sched->varena_used, nv);
+                                }
+                                base = __shfl_sync(0xffffffffu, base, 0);
+                                if (fviol) {
+                                    const uint64_t idx = base + __popc(vb & ((1u << lane) - 1u));
+                                    if (D->viol) {
+                                        if (idx < D->viol_cap) {
+                                            int32_t* outp = D->viol + idx * k;
+                                            for (int q = 0; q < k; q++) outp[D->order[q]] = (int32_t)level_vertex(mo, q, L, fv);
+                                        }
+                                    } else if (idx < A.sched->varena_cap) {
+                                        int32_t* rec = A.sched->varena + idx * A.sched->vstride;
+                                        rec[0] = s;
+                                        for (int q = 0; q < k; q++) rec[1 + D->order[q]] = (int32_t)level_vertex(mo, q, L, fv);
+                                    }
+                                }
+                            }
+                        }
+                    }
                 }
                 cn.iteration(LAST);
             }
-            if (LAST) {
+            if (LAST || fuse) {
                 const unsigned long long tm = __reduce_add_sync(0xffffffffu, tile_matches);
                 if (lane == 0 && tm) atomicAdd((unsigned long long*)&S->n_matches, tm);
             }
