@@ -165,7 +165,7 @@ __device__ __forceinline__ bool lit_holds_at(const DevGraph& g, const DevLit& L,
 // Partial matches of the second-to-last level with at most this many
 // candidates at the last level are expanded by the warp that makes them,
 // without being stored.
-constexpr uint32_t FUSE_FANOUT = 64;
+constexpr uint32_t FUSE_FANOUT = 32;
 
 // Largest r in [0, n) with S[r] <= w (S non-decreasing, S[0] <= w). The index
 // offsets are read-only during enumeration; the frontier prefix is rewritten

@@ -26,8 +26,8 @@ namespace gfd {
 namespace {
 
 constexpr int FILTER_THREADS = 256;
-constexpr int COMPACT_THREADS = 1024;
-constexpr uint32_t COMPACT_WORDS = 4096;  // words (or counts) per chunk
+constexpr int COMPACT_THREADS = 256;
+constexpr uint32_t COMPACT_WORDS = 1024;  // words (or counts) per chunk
 constexpr int WARP_KERNEL_THREADS = 256;
 
 __device__ __forceinline__ uint64_t gwarp_id() {
@@ -75,14 +75,21 @@ __global__ void k_filter(DevGraph g, const FilterKey* __restrict__ keys, int nke
     }
 }
 
-__global__ void k_and(DevGraph g, const AndJob* __restrict__ jobs, int njobs) {
-    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
-    for (int j = 0; j < njobs; j++) {
-        const AndJob J = jobs[j];
-        for (uint64_t w = (tid + (uint64_t)j * 7919) % nt; w < g.nwords; w += nt) {
+// One block per (job, chunk of AND_WORDS words) item, so that every job's words
+// are spread over the GPU and no thread walks the job table.
+constexpr uint32_t AND_WORDS = 2048;
+constexpr int AND_THREADS = 256;
+
+__global__ void __launch_bounds__(AND_THREADS) k_and(DevGraph g, const AndJob* __restrict__ jobs, int njobs,
+                                                      uint32_t nchunks) {
+    for (uint64_t it = blockIdx.x; it < (uint64_t)njobs * nchunks; it += gridDim.x) {
+        const AndJob& J = jobs[it / nchunks];
+        const uint32_t w0 = (uint32_t)(it % nchunks) * AND_WORDS;
+        const uint32_t w1 = min(g.nwords, w0 + AND_WORDS);
+        const int ntmp = J.ntmp;
+        for (uint32_t w = w0 + threadIdx.x; w < w1; w += AND_THREADS) {
             uint32_t x = J.src[w];
-            for (int t = 0; t < J.ntmp; t++) x &= J.tmp[t][w];
+            for (int t = 0; t < ntmp; t++) x &= J.tmp[t][w];
             J.bm[w] = x;
         }
     }
@@ -706,8 +713,10 @@ int launch_filter(const DevGraph& g, const FilterKey* d_keys, int nkeys, uint32_
 }
 
 int launch_and(const DevGraph& g, const AndJob* d_jobs, int njobs, cudaStream_t st) {
-    if (njobs <= 0) return GFD_OK;
-    k_and<<<grid_warps(4), 256, 0, st>>>(g, d_jobs, njobs);
+    if (njobs <= 0 || g.nwords == 0) return GFD_OK;
+    const uint32_t nch = (g.nwords + AND_WORDS - 1) / AND_WORDS;
+    const int grid = (int)std::min<uint64_t>((uint64_t)njobs * nch, 152 * 16);
+    k_and<<<grid, AND_THREADS, 0, st>>>(g, d_jobs, njobs, nch);
     return check_launch("k_and");
 }
 
@@ -718,7 +727,7 @@ uint32_t compact_chunks(const DevGraph& g) {
 int launch_compact(const DevGraph& g, const CompactJob* d_jobs, int njobs, cudaStream_t st) {
     if (njobs <= 0) return GFD_OK;
     const uint32_t nch = compact_chunks(g);
-    const int grid = (int)std::min<uint64_t>((uint64_t)njobs * nch, 152 * 2);
+    const int grid = (int)std::min<uint64_t>((uint64_t)njobs * nch, 152 * 8);
     k_compact_sums<<<grid, COMPACT_THREADS, 0, st>>>(g, d_jobs, njobs, nch);
     k_compact_write<<<grid, COMPACT_THREADS, 0, st>>>(g, d_jobs, njobs, nch);
     return check_launch("k_compact");
@@ -758,7 +767,7 @@ int launch_cpi_count(const DevGraph& g, const CpiJob* d_jobs, int njobs, uint32_
     if (hq.scan) k_cpi_count<true><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
     else k_cpi_count<false><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
     k_cpi_count_hub<<<HUB_GRID, HUB_THREADS, 0, st>>>(g, d_jobs, hq);
-    const int grid = (int)std::min<uint64_t>((uint64_t)njobs * nchunks, 152 * 4);
+    const int grid = (int)std::min<uint64_t>((uint64_t)njobs * nchunks, 152 * 8);
     k_cpi_sums<<<grid, COMPACT_THREADS, 0, st>>>(d_jobs, njobs, nchunks);
     k_cpi_scan<<<grid, COMPACT_THREADS, 0, st>>>(d_jobs, njobs, nchunks, d_err);
     k_cpi_totals<<<(njobs + 255) / 256, 256, 0, st>>>(d_jobs, njobs, d_totals);
