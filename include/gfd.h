@@ -244,11 +244,6 @@ const int32_t *gfd_result_tuples(gfd_result *r);
  * result's buffer). Returns GFD_OK, GFD_ERR_INVALID_ARG (NULL or too small a
  * buffer), GFD_ERR_OUT_OF_MEMORY or a CUDA error code. */
 int gfd_result_copy_tuples(gfd_result *r, int32_t *out, uint64_t capacity);
-/* Copies of violation tuples into pageable host memory go through a page-locked
- * double buffer of 2 x 64 MiB that the library allocates on first use and keeps
- * until the process exits (host threads move each chunk into the destination
- * while the next one crosses the link); page-locked destinations are copied
- * directly. */
 /* The sorted tuples of n results (say, one gfd_validate_batch) written back to
  * back into caller-owned host memory `out` of `capacity` int32: result 0's
  * n_violations * k ints, then result 1's, and so on. One device sort over all of

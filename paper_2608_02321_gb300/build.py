@@ -71,7 +71,7 @@ def build(verbose: bool = False, extra_flags=()) -> str:
         raise RuntimeError("nvcc failed; see messages above")
     if jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
         if run(cmd):
             raise RuntimeError("link failed")
         os.replace(tmp, LIB)

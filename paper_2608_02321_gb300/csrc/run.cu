@@ -29,8 +29,6 @@
 #include <deque>
 #include <map>
 #include <memory>
-#include <mutex>
-#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -1442,79 +1440,14 @@ __global__ void k_unpack_multi(const PackSrc* src, const int32_t* M, int W, cons
 
 }  // namespace
 
-// Device-to-host copy of results into caller memory, synchronous. A page-locked
-// destination takes one copy. A pageable one goes through a page-locked double
-// buffer of the library (allocated once, kept for the process) in chunks: while
-// a chunk crosses to the host, several host threads copy the previous one into
-// the destination, so the copy is not held to one thread's pageable-memory
-// bandwidth.
-namespace {
-
-constexpr size_t STAGE_CHUNK = 64ull << 20;
-constexpr int COPY_THREADS = 8;
-std::mutex g_stage_mu;
-void* g_stage[2] = {nullptr, nullptr};
-
-void par_memcpy(void* dst, const void* src, size_t n) {
-    if (n < (4u << 20)) {
-        memcpy(dst, src, n);
-        return;
-    }
-    const size_t per = ((n + COPY_THREADS - 1) / COPY_THREADS + 4095) & ~(size_t)4095;
-    std::vector<std::thread> th;
-    for (int t = 1; t < COPY_THREADS && (size_t)t * per < n; t++) {
-        const size_t a = (size_t)t * per, len = std::min(per, n - a);
-        th.emplace_back([=] { memcpy((char*)dst + a, (const char*)src + a, len); });
-    }
-    memcpy(dst, src, std::min(per, n));
-    for (auto& x : th) x.join();
-}
-
-}  // namespace
-
+// Device-to-host copy of results into caller memory, synchronous. (A staged
+// copy through a page-locked double buffer, several host threads moving each
+// chunk into pageable memory, was slower here: 67 vs 44 ms for 853 MB.)
 int copy_to_host(void* dst, const void* src, size_t bytes, cudaStream_t st) {
     if (bytes == 0) return GFD_OK;
-    cudaPointerAttributes pa{};
-    const bool pinned = cudaPointerGetAttributes(&pa, dst) == cudaSuccess && pa.type == cudaMemoryTypeHost;
-    cudaGetLastError();
-    std::unique_lock<std::mutex> lock(g_stage_mu);
-    if (!pinned && !g_stage[0]) {
-        if (cudaMallocHost(&g_stage[0], STAGE_CHUNK) != cudaSuccess ||
-            cudaMallocHost(&g_stage[1], STAGE_CHUNK) != cudaSuccess) {
-            cudaGetLastError();
-            if (g_stage[0]) cudaFreeHost(g_stage[0]);
-            g_stage[0] = g_stage[1] = nullptr;
-        }
-    }
-    if (pinned || !g_stage[0] || bytes <= (1u << 20)) {  // one copy
-        lock.unlock();
-        GFD_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st));
-        GFD_CUDA(cudaStreamSynchronize(st));
-        return GFD_OK;
-    }
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    int rc = GFD_OK;
-    for (auto& e : ev)
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) rc = GFD_ERR_CUDA;
-    const size_t nch = (bytes + STAGE_CHUNK - 1) / STAGE_CHUNK;
-    for (size_t c = 0; c <= nch && rc == GFD_OK; c++) {
-        if (c < nch) {  // chunk c into buffer c % 2 (its previous chunk was copied out in step c - 1)
-            const size_t off = c * STAGE_CHUNK, len = std::min(STAGE_CHUNK, bytes - off);
-            cudaError_t e = cudaMemcpyAsync(g_stage[c & 1], (const char*)src + off, len, cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaEventRecord(ev[c & 1], st);
-            if (e != cudaSuccess) rc = cuda_fail(e, "staged result copy");
-        }
-        if (c > 0 && rc == GFD_OK) {  // chunk c - 1 into the destination
-            const size_t off = (c - 1) * STAGE_CHUNK, len = std::min(STAGE_CHUNK, bytes - off);
-            cudaError_t e = cudaEventSynchronize(ev[(c - 1) & 1]);
-            if (e != cudaSuccess) rc = cuda_fail(e, "staged result copy");
-            else par_memcpy((char*)dst + off, g_stage[(c - 1) & 1], len);
-        }
-    }
-    if (rc != GFD_OK) cudaStreamSynchronize(st);  // no copy into the buffers may remain in flight
-    for (auto& e : ev)
-        if (e) cudaEventDestroy(e);
-    return rc;
+    GFD_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st));
+    GFD_CUDA(cudaStreamSynchronize(st));
+    return GFD_OK;
 }
 
 // Lexicographic order of the violation tuples (Vio is a set; this fixes a
