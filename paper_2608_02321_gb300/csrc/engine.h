@@ -117,6 +117,9 @@ struct HubQueue {
     // counting pass: [0] candidates whose adjacency was scanned, [1] adjacency
     // entries read (null: not counting)
     unsigned long long* scan;
+    // room for the exclusive prefix of a launch's per-job group counts (one
+    // more than the largest job table of the group)
+    uint32_t* jpre;
 };
 
 // ---- index kernels (index.cu); each launch covers all jobs given

@@ -193,6 +193,48 @@ __device__ __forceinline__ bool hub_push(const HubQueue& q, bool want, unsigned 
 
 __device__ __forceinline__ uint32_t hub_count(const HubQueue& q) { return min(*q.n, q.cap); }
 
+// The adjacency kernels below take (job, group of 32 candidates) items from one
+// flat index: k_job_groups writes the exclusive prefix of the jobs' group
+// counts (total at [njobs]), and job_of finds an item's job by binary search,
+// so no warp walks the whole job table.
+__device__ __forceinline__ uint32_t job_count(const ScatterJob& J) { return *J.qcount; }
+__device__ __forceinline__ uint32_t job_count(const PruneJob& J) { return *J.count; }
+__device__ __forceinline__ uint32_t job_count(const CpiJob& J) { return *J.pcount; }
+
+constexpr int JOB_SCAN_THREADS = 1024;
+
+template <typename Job>
+__global__ void __launch_bounds__(JOB_SCAN_THREADS) k_job_groups(const Job* __restrict__ jobs, int njobs,
+                                                                  uint32_t* pre) {
+    using Scan = cub::BlockScan<uint32_t, JOB_SCAN_THREADS>;
+    __shared__ typename Scan::TempStorage tmp;
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b = 0; b < njobs; b += JOB_SCAN_THREADS) {
+        const int j = b + threadIdx.x;
+        const uint32_t groups = j < njobs ? (job_count(jobs[j]) + 31) / 32 : 0;
+        uint32_t excl, total;
+        Scan(tmp).ExclusiveSum(groups, excl, total);
+        if (j < njobs) pre[j] = carry + excl;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) pre[njobs] = carry;
+}
+
+// the job whose items [pre[j], pre[j+1]) hold item it (pre[njobs] > it)
+__device__ __forceinline__ int job_of(const uint32_t* pre, int njobs, uint32_t it) {
+    int lo = 0, hi = njobs;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(pre + mid) <= it) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // Counting pass: add this thread's scanned candidates and adjacency entries to
 // the run's counters (all lanes of the warp call it; one atomic per warp).
 template <bool COUNT>
@@ -218,13 +260,16 @@ __global__ void k_scatter(DevGraph g, const ScatterJob* __restrict__ jobs, int n
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
     uint64_t sc = 0, se = 0;
-    for (int j = 0; j < njobs; j++) {
+    const uint32_t ngroups = hq.jpre[njobs];
+    for (uint64_t it = gw; it < ngroups; it += nw) {
+        // the warp's group of 32 candidates: job j, group grp of that job
+        const int j = job_of(hq.jpre, njobs, (uint32_t)it);
+        const uint64_t grp = it - hq.jpre[j];
         const ScatterJob J = jobs[j];
         const uint32_t n = *J.qcount;
         const uint32_t* off = J.scan_out ? g.out_off : g.in_off;
         const uint32_t* adj = J.scan_out ? g.out_adj : g.in_adj;
-        const uint64_t groups = (n + 31) / 32;
-        for (uint64_t grp = (gw + (uint64_t)j * 7919) % nw; grp < groups; grp += nw) {
+        {
             const uint64_t a = grp * 32 + lane;
             uint32_t e0 = 0, e1 = 0;
             if (a < n) {
@@ -304,12 +349,15 @@ __global__ void k_prune(DevGraph g, const PruneJob* __restrict__ jobs, int njobs
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
     uint64_t sc = 0, se = 0;
-    for (int j = 0; j < njobs; j++) {
+    const uint32_t ngroups = hq.jpre[njobs];
+    for (uint64_t it = gw; it < ngroups; it += nw) {
+        // the warp's group of 32 candidates: job j, group grp of that job
+        const int j = job_of(hq.jpre, njobs, (uint32_t)it);
+        const uint64_t grp = it - hq.jpre[j];
         const PruneJob& J = jobs[j];
         const uint32_t n = *J.count;
         const int ncon = J.ncon;
-        const uint64_t groups = (n + 31) / 32;
-        for (uint64_t grp = (gw + (uint64_t)j * 7919) % nw; grp < groups; grp += nw) {
+        {
             const uint64_t a = grp * 32 + lane;
             const bool valid = a < n;
             const uint32_t v = valid ? (uint32_t)J.cand[a] : 0u;
@@ -348,13 +396,16 @@ __global__ void k_cpi_count(DevGraph g, const CpiJob* __restrict__ jobs, int njo
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
     uint64_t sc = 0, se = 0;
-    for (int j = 0; j < njobs; j++) {
+    const uint32_t ngroups = hq.jpre[njobs];
+    for (uint64_t it = gw; it < ngroups; it += nw) {
+        // the warp's group of 32 candidates: job j, group grp of that job
+        const int j = job_of(hq.jpre, njobs, (uint32_t)it);
+        const uint64_t grp = it - hq.jpre[j];
         const CpiJob J = jobs[j];
         const uint32_t n = *J.pcount;
         const uint32_t* off = J.out ? g.out_off : g.in_off;
         const uint32_t* adj = J.out ? g.out_adj : g.in_adj;
-        const uint64_t groups = (n + 31) / 32;
-        for (uint64_t grp = (gw + (uint64_t)j * 7919) % nw; grp < groups; grp += nw) {
+        {
             const uint64_t a = grp * 32 + lane;
             uint32_t e0 = 0, e1 = 0;
             if (a < n) {
@@ -471,13 +522,16 @@ __global__ void k_cpi_fill(DevGraph g, const CpiJob* __restrict__ jobs, int njob
     const int lane = threadIdx.x & 31;
     const uint64_t gw = gwarp_id(), nw = nwarps_total();
     uint64_t sc = 0, se = 0;
-    for (int j = 0; j < njobs; j++) {
+    const uint32_t ngroups = hq.jpre[njobs];
+    for (uint64_t it = gw; it < ngroups; it += nw) {
+        // the warp's group of 32 candidates: job j, group grp of that job
+        const int j = job_of(hq.jpre, njobs, (uint32_t)it);
+        const uint64_t grp = it - hq.jpre[j];
         const CpiJob J = jobs[j];
         const uint32_t n = *J.pcount;
         const uint32_t* off = J.out ? g.out_off : g.in_off;
         const uint32_t* adj = J.out ? g.out_adj : g.in_adj;
-        const uint64_t groups = (n + 31) / 32;
-        for (uint64_t grp = (gw + (uint64_t)j * 7919) % nw; grp < groups; grp += nw) {
+        {
             const uint64_t a = grp * 32 + lane;
             uint32_t e0 = 0, e1 = 0, o = 0, oend = 0;
             if (a < n) {
@@ -741,6 +795,7 @@ static int hub_reset(const HubQueue& hq, cudaStream_t st) {
 int launch_scatter(const DevGraph& g, const ScatterJob* d_jobs, int njobs, const HubQueue& hq, cudaStream_t st) {
     if (njobs <= 0) return GFD_OK;
     if (int rc = hub_reset(hq, st)) return rc;
+    k_job_groups<ScatterJob><<<1, JOB_SCAN_THREADS, 0, st>>>(d_jobs, njobs, hq.jpre);
     if (hq.scan) k_scatter<true><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
     else k_scatter<false><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
     k_scatter_hub<<<HUB_GRID, HUB_THREADS, 0, st>>>(g, d_jobs, hq);
@@ -750,6 +805,7 @@ int launch_scatter(const DevGraph& g, const ScatterJob* d_jobs, int njobs, const
 int launch_prune(const DevGraph& g, const PruneJob* d_jobs, int njobs, const HubQueue& hq, cudaStream_t st) {
     if (njobs <= 0) return GFD_OK;
     if (int rc = hub_reset(hq, st)) return rc;
+    k_job_groups<PruneJob><<<1, JOB_SCAN_THREADS, 0, st>>>(d_jobs, njobs, hq.jpre);
     if (hq.scan) k_prune<true><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
     else k_prune<false><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
     k_prune_hub<<<HUB_GRID, HUB_THREADS, 0, st>>>(g, d_jobs, hq);
@@ -764,6 +820,7 @@ int launch_cpi_count(const DevGraph& g, const CpiJob* d_jobs, int njobs, uint32_
                      uint32_t* d_totals, const HubQueue& hq, cudaStream_t st) {
     if (njobs <= 0) return GFD_OK;
     if (int rc = hub_reset(hq, st)) return rc;
+    k_job_groups<CpiJob><<<1, JOB_SCAN_THREADS, 0, st>>>(d_jobs, njobs, hq.jpre);
     if (hq.scan) k_cpi_count<true><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
     else k_cpi_count<false><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
     k_cpi_count_hub<<<HUB_GRID, HUB_THREADS, 0, st>>>(g, d_jobs, hq);
@@ -777,6 +834,7 @@ int launch_cpi_count(const DevGraph& g, const CpiJob* d_jobs, int njobs, uint32_
 int launch_cpi_fill(const DevGraph& g, const CpiJob* d_jobs, int njobs, const HubQueue& hq, cudaStream_t st) {
     if (njobs <= 0) return GFD_OK;
     if (int rc = hub_reset(hq, st)) return rc;
+    k_job_groups<CpiJob><<<1, JOB_SCAN_THREADS, 0, st>>>(d_jobs, njobs, hq.jpre);
     if (hq.scan) k_cpi_fill<true><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
     else k_cpi_fill<false><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
     k_cpi_fill_hub<<<HUB_GRID, HUB_THREADS, 0, st>>>(g, d_jobs, hq);

@@ -223,6 +223,7 @@ struct Group {
     std::vector<Off> offs;
     size_t o_keybm = 0, o_keys = 0, o_tmp = 0, o_cmp_sums = 0, o_cpi_sums = 0, o_cpi_tot = 0;
     size_t o_hubq = 0, o_hubn = 0;  // hub queue of the adjacency kernels
+    size_t o_jpre = 0;               // per-launch prefix of the jobs' group counts
     uint8_t* cpi_base = nullptr;  // index edges, sized after counting
     size_t cpi_bytes = 0;
     size_t cpi_bound = 0;  // upper bound of cpi_bytes known at planning time
@@ -384,6 +385,7 @@ int group_plan(gfd_graph* g, const gfd_gfd* const* phis, int n, const gfd_opts* 
     G->o_cpi_tot = L.take(4ull * std::max<size_t>(1, n_cpi));
     G->o_hubq = L.take(8ull * HUB_CAP);
     G->o_hubn = L.take(4);
+    G->o_jpre = L.take(4ull * (std::max(n_sct, std::max(n_prn, n_cpi)) + 1));
     // the region uploaded from the host: keys and job tables
     G->o_jobs = L.size;
     G->o_keys = L.take(sizeof(FilterKey) * std::max(1, nkeys));
@@ -630,7 +632,8 @@ int group_launch(gfd_graph* g, Group* G, const Tables& T, cudaMemPool_t pool, cu
     const DevGraph& dg = g->dg;
     uint8_t* base = G->base;
     const HubQueue hq{(unsigned long long*)(base + G->o_hubq), (uint32_t*)(base + G->o_hubn), HUB_CAP,
-                      count ? (unsigned long long*)&T.sched->cnt[CNT_SCAN_CANDS] : nullptr};
+                      count ? (unsigned long long*)&T.sched->cnt[CNT_SCAN_CANDS] : nullptr,
+                      (uint32_t*)(base + G->o_jpre)};
     prof.begin(PROF_FILTER, st);
     if (int rc = launch_filter(dg, (const FilterKey*)(base + G->o_keys), (int)G->keys.size(),
                                (uint32_t*)(base + G->o_keybm), st))
