@@ -143,6 +143,7 @@ struct SlotState {
     uint64_t n_matches;
     uint64_t n_viol;
     uint64_t st_work, st_rows, st_probes, st_steps, st_cpi;
+    uint32_t tile;            // work items per tile in the current step
 };
 
 // Counters of the counting pass (GFD_FLAG_COUNT): what one run's kernels

@@ -166,6 +166,8 @@ __device__ __forceinline__ bool lit_holds_at(const DevGraph& g, const DevLit& L,
 // candidates at the last level are expanded by the warp that makes them,
 // without being stored.
 constexpr uint32_t FUSE_FANOUT = 32;
+// Tiles of a step that fuses the last level are this many times smaller.
+constexpr uint64_t FUSED_TILE_DIV = 2;
 
 // Largest r in [0, n) with S[r] <= w (S non-decreasing, S[0] <= w). The index
 // offsets are read-only during enumeration; the frontier prefix is rewritten
@@ -286,7 +288,6 @@ __device__ void expand_warps(const EnumArgs& A) {
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const DevGraph& g = A.g;
     const uint32_t total_tiles = *(volatile uint32_t*)&A.sched->total_tiles;
-    const uint64_t tile = *(volatile uint32_t*)&A.sched->tile;  // work items per tile in this step
     uint32_t probes = 0;  // a statistic (saturates per warp)
     for (uint64_t t = gwarp; t < total_tiles;) {
         cn.mark();
@@ -298,6 +299,7 @@ __device__ void expand_warps(const EnumArgs& A) {
         const int l = __ldcg(&S->cur);
         const int i = k == 1 ? 0 : l + 1;  // level being matched
         const bool last = i == k - 1;
+        const uint64_t tile = __ldcg(&S->tile);  // work items per tile of this slot in this step
         const uint64_t wb = __ldcg((const unsigned long long*)&S->cb) + (t - __ldcg(A.tile_base + s)) * tile;
         const uint64_t we = min(wb + tile, (uint64_t)__ldcg((const unsigned long long*)&S->ce));
         const LevelPlan& LP = D->lv[i];
@@ -939,12 +941,22 @@ __device__ void control_step(const EnumArgs& A, bool first) {
         const uint64_t per = work_s / (4ull * (uint64_t)A.n_warps);
         tile = min(tile, max((uint64_t)32, (uint64_t)((per + 31) & ~(uint64_t)31)));
     }
+    // A slot whose step makes the second-to-last level's partial matches also
+    // expands most of their last level inside the same tiles (fused, up to
+    // FUSE_FANOUT items per partial match): its tiles are cut smaller, so that
+    // no single tile holds the step's end.
+    const uint64_t tile_fused = max((uint64_t)32, (tile / FUSED_TILE_DIV) & ~(uint64_t)31);
     for (int base = 0; base < A.n_slots; base += CT) {
         const int s = base + threadIdx.x;
         uint32_t tiles = 0;
         if (s < A.n_slots) {
-            const SlotState* S = A.state + s;
-            if (S->cur >= 0) tiles = (uint32_t)((S->ce - S->cb + tile - 1) / tile);
+            SlotState* S = A.state + s;
+            if (S->cur >= 0) {
+                const int k = A.slots[s].k;
+                const uint64_t ts = k >= 3 && S->cur + 1 == k - 2 ? tile_fused : tile;
+                S->tile = (uint32_t)ts;
+                tiles = (uint32_t)((S->ce - S->cb + ts - 1) / ts);
+            }
         }
         uint32_t excl, total;
         Scan(tmp).ExclusiveSum(tiles, excl, total);
