@@ -19,6 +19,9 @@
 // items of each job with a per-job rotation so that small jobs spread out.
 #include <cub/cub.cuh>
 
+#include <map>
+#include <mutex>
+
 #include "engine.h"
 
 namespace gfd {
@@ -172,7 +175,6 @@ constexpr uint32_t SHORT_LIST = 32;
 constexpr int UNROLL = 4;
 
 constexpr int HUB_THREADS = 512;
-constexpr int HUB_GRID = 152 * 4;  // blocks of the hub kernels (grid-stride over the queue)
 
 // Queue the lanes whose list is a hub (warp-synchronous: every lane calls it);
 // true for the lanes whose item was stored.
@@ -737,7 +739,34 @@ __global__ void k_cpi_totals(const CpiJob* __restrict__ jobs, int njobs, uint32_
     if (j < njobs) totals[j] = jobs[j].off[*jobs[j].pcount];
 }
 
-int grid_warps(int sms_mult = 8) { return 152 * sms_mult; }
+// Blocks of a grid-stride kernel: as many as the device holds at once. A
+// larger grid leaves a partial second wave, whose blocks start only as
+// first-wave blocks exit and then run their share at a fraction of the
+// occupancy. Cached per (kernel, device).
+int resident_grid(const void* fn, int threads) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(fn, dev);
+    const auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();  // the launch itself reports a kernel that cannot run
+        per_sm = 1;
+    }
+    const int grid = std::max(1, sms) * per_sm;
+    cache.emplace(key, grid);
+    return grid;
+}
+
+template <typename F>
+int grid_of(F* fn, int threads) {
+    return resident_grid((const void*)fn, threads);
+}
 
 int check_launch(const char* what) {
     cudaError_t e = cudaGetLastError();
@@ -796,9 +825,9 @@ int launch_scatter(const DevGraph& g, const ScatterJob* d_jobs, int njobs, const
     if (njobs <= 0) return GFD_OK;
     if (int rc = hub_reset(hq, st)) return rc;
     k_job_groups<ScatterJob><<<1, JOB_SCAN_THREADS, 0, st>>>(d_jobs, njobs, hq.jpre);
-    if (hq.scan) k_scatter<true><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
-    else k_scatter<false><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
-    k_scatter_hub<<<HUB_GRID, HUB_THREADS, 0, st>>>(g, d_jobs, hq);
+    if (hq.scan) k_scatter<true><<<grid_of(k_scatter<true>, WARP_KERNEL_THREADS), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    else k_scatter<false><<<grid_of(k_scatter<false>, WARP_KERNEL_THREADS), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    k_scatter_hub<<<grid_of(k_scatter_hub, HUB_THREADS), HUB_THREADS, 0, st>>>(g, d_jobs, hq);
     return check_launch("k_scatter");
 }
 
@@ -806,9 +835,9 @@ int launch_prune(const DevGraph& g, const PruneJob* d_jobs, int njobs, const Hub
     if (njobs <= 0) return GFD_OK;
     if (int rc = hub_reset(hq, st)) return rc;
     k_job_groups<PruneJob><<<1, JOB_SCAN_THREADS, 0, st>>>(d_jobs, njobs, hq.jpre);
-    if (hq.scan) k_prune<true><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
-    else k_prune<false><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
-    k_prune_hub<<<HUB_GRID, HUB_THREADS, 0, st>>>(g, d_jobs, hq);
+    if (hq.scan) k_prune<true><<<grid_of(k_prune<true>, WARP_KERNEL_THREADS), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    else k_prune<false><<<grid_of(k_prune<false>, WARP_KERNEL_THREADS), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    k_prune_hub<<<grid_of(k_prune_hub, HUB_THREADS), HUB_THREADS, 0, st>>>(g, d_jobs, hq);
     return check_launch("k_prune");
 }
 
@@ -821,9 +850,9 @@ int launch_cpi_count(const DevGraph& g, const CpiJob* d_jobs, int njobs, uint32_
     if (njobs <= 0) return GFD_OK;
     if (int rc = hub_reset(hq, st)) return rc;
     k_job_groups<CpiJob><<<1, JOB_SCAN_THREADS, 0, st>>>(d_jobs, njobs, hq.jpre);
-    if (hq.scan) k_cpi_count<true><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
-    else k_cpi_count<false><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
-    k_cpi_count_hub<<<HUB_GRID, HUB_THREADS, 0, st>>>(g, d_jobs, hq);
+    if (hq.scan) k_cpi_count<true><<<grid_of(k_cpi_count<true>, WARP_KERNEL_THREADS), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    else k_cpi_count<false><<<grid_of(k_cpi_count<false>, WARP_KERNEL_THREADS), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    k_cpi_count_hub<<<grid_of(k_cpi_count_hub, HUB_THREADS), HUB_THREADS, 0, st>>>(g, d_jobs, hq);
     const int grid = (int)std::min<uint64_t>((uint64_t)njobs * nchunks, 152 * 8);
     k_cpi_sums<<<grid, COMPACT_THREADS, 0, st>>>(d_jobs, njobs, nchunks);
     k_cpi_scan<<<grid, COMPACT_THREADS, 0, st>>>(d_jobs, njobs, nchunks, d_err);
@@ -835,9 +864,9 @@ int launch_cpi_fill(const DevGraph& g, const CpiJob* d_jobs, int njobs, const Hu
     if (njobs <= 0) return GFD_OK;
     if (int rc = hub_reset(hq, st)) return rc;
     k_job_groups<CpiJob><<<1, JOB_SCAN_THREADS, 0, st>>>(d_jobs, njobs, hq.jpre);
-    if (hq.scan) k_cpi_fill<true><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
-    else k_cpi_fill<false><<<grid_warps(), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
-    k_cpi_fill_hub<<<HUB_GRID, HUB_THREADS, 0, st>>>(g, d_jobs, hq);
+    if (hq.scan) k_cpi_fill<true><<<grid_of(k_cpi_fill<true>, WARP_KERNEL_THREADS), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    else k_cpi_fill<false><<<grid_of(k_cpi_fill<false>, WARP_KERNEL_THREADS), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
+    k_cpi_fill_hub<<<grid_of(k_cpi_fill_hub, HUB_THREADS), HUB_THREADS, 0, st>>>(g, d_jobs, hq);
     return check_launch("k_cpi_fill");
 }
 
