@@ -291,7 +291,9 @@ __device__ void expand_warps(const EnumArgs& A) {
     uint32_t probes = 0;  // a statistic (saturates per warp)
     for (uint64_t t = gwarp; t < total_tiles;) {
         cn.mark();
-        const int s = (int)warp_find(A.tile_base, 0, (uint64_t)A.n_slots, t, lane);
+        // the step's tiles: those of fusing slots first, then the others
+        const uint32_t* tb = t < __ldcg(A.tile_base + A.n_slots) ? A.tile_base : A.tile_base + A.n_slots + 1;
+        const int s = (int)warp_find(tb, 0, (uint64_t)A.n_slots, t, lane);
         const SlotDesc* __restrict__ D = A.slots + s;
         SlotState* S = A.state + s;
         const int k = D->k;
@@ -300,7 +302,7 @@ __device__ void expand_warps(const EnumArgs& A) {
         const int i = k == 1 ? 0 : l + 1;  // level being matched
         const bool last = i == k - 1;
         const uint64_t tile = __ldcg(&S->tile);  // work items per tile of this slot in this step
-        const uint64_t wb = __ldcg((const unsigned long long*)&S->cb) + (t - __ldcg(A.tile_base + s)) * tile;
+        const uint64_t wb = __ldcg((const unsigned long long*)&S->cb) + (t - __ldcg(tb + s)) * tile;
         const uint64_t we = min(wb + tile, (uint64_t)__ldcg((const unsigned long long*)&S->ce));
         const LevelPlan& LP = D->lv[i];
         const int nchk = LP.nchk;
@@ -874,9 +876,9 @@ __device__ void slot_start(const SlotDesc* D, SlotState* S) {
 // One block: finish the last step of every slot and plan the next one.
 template <int CT>
 __device__ void control_step(const EnumArgs& A, bool first) {
-    using Scan = cub::BlockScan<uint32_t, CT>;
+    using Scan = cub::BlockScan<unsigned long long, CT>;
     __shared__ typename Scan::TempStorage tmp;
-    __shared__ uint32_t carry_s;
+    __shared__ unsigned long long carry_s;
     __shared__ int32_t active_s;
     __shared__ int32_t expired_s;
     __shared__ unsigned long long work_s;
@@ -944,30 +946,42 @@ __device__ void control_step(const EnumArgs& A, bool first) {
     // A slot whose step makes the second-to-last level's partial matches also
     // expands most of their last level inside the same tiles (fused, up to
     // FUSE_FANOUT items per partial match): its tiles are cut smaller, so that
-    // no single tile holds the step's end.
+    // no single tile holds the step's end, and are numbered before the step's
+    // other tiles, so that the heaviest are handed out first. tile_base holds
+    // two prefixes over the slots: [0, n] of the fusing slots' tiles (F in
+    // all), [n + 1, 2n + 1] of the others', from F on. One scan of both counts
+    // packed in 64 bits (each total is below 2^32).
     const uint64_t tile_fused = max((uint64_t)32, (tile / FUSED_TILE_DIV) & ~(uint64_t)31);
     for (int base = 0; base < A.n_slots; base += CT) {
         const int s = base + threadIdx.x;
-        uint32_t tiles = 0;
+        unsigned long long tiles = 0;  // fused << 32 | other
         if (s < A.n_slots) {
             SlotState* S = A.state + s;
             if (S->cur >= 0) {
                 const int k = A.slots[s].k;
-                const uint64_t ts = k >= 3 && S->cur + 1 == k - 2 ? tile_fused : tile;
+                const bool fused = k >= 3 && S->cur + 1 == k - 2;
+                const uint64_t ts = fused ? tile_fused : tile;
                 S->tile = (uint32_t)ts;
-                tiles = (uint32_t)((S->ce - S->cb + ts - 1) / ts);
+                const uint64_t nt = (S->ce - S->cb + ts - 1) / ts;
+                tiles = fused ? nt << 32 : nt;
             }
         }
-        uint32_t excl, total;
+        unsigned long long excl, total;
         Scan(tmp).ExclusiveSum(tiles, excl, total);
-        if (s < A.n_slots) A.tile_base[s] = carry_s + excl;
+        if (s < A.n_slots) {
+            A.tile_base[s] = (uint32_t)((carry_s + excl) >> 32);
+            A.tile_base[A.n_slots + 1 + s] = (uint32_t)(carry_s + excl);  // F added below
+        }
         __syncthreads();
         if (threadIdx.x == 0) carry_s += total;
         __syncthreads();
     }
+    const uint32_t nfused = (uint32_t)(carry_s >> 32), nother = (uint32_t)carry_s;
+    for (int s = threadIdx.x; s < A.n_slots; s += CT) A.tile_base[A.n_slots + 1 + s] += nfused;
     if (threadIdx.x == 0) {
-        A.tile_base[A.n_slots] = carry_s;
-        A.sched->total_tiles = carry_s;
+        A.tile_base[A.n_slots] = nfused;
+        A.tile_base[2 * A.n_slots + 1] = nfused + nother;
+        A.sched->total_tiles = nfused + nother;
         A.sched->tile = (uint32_t)tile;
         A.sched->tile_next = 0;
         A.sched->active = active_s;
