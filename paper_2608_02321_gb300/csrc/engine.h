@@ -142,7 +142,7 @@ struct EnumArgs {
     const SlotDesc* slots;
     SlotState* state;
     Sched* sched;
-    uint32_t* tile_base;  // [2 (n_slots + 1)]: fusing slots' tile prefix, then the others'
+    uint32_t* tile_base;  // [3 (n_slots + 1)]: tile prefixes of the fusing, intermediate, last-level slots
     int32_t n_slots;
     int32_t tile;         // largest number of work items per tile
     int32_t n_warps;      // warps of the expansion grid (0: unknown, tiles of `tile`)

@@ -165,9 +165,12 @@ __device__ __forceinline__ bool lit_holds_at(const DevGraph& g, const DevLit& L,
 // Partial matches of the second-to-last level with at most this many
 // candidates at the last level are expanded by the warp that makes them,
 // without being stored.
-constexpr uint32_t FUSE_FANOUT = 32;
+constexpr uint32_t FUSE_FANOUT = 64;
 // Tiles of a step that fuses the last level are this many times smaller.
 constexpr uint64_t FUSED_TILE_DIV = 2;
+// Number the last level's tiles after the other intermediate levels' (else
+// both are numbered together, in slot order).
+constexpr bool LAST_LEVEL_TILES_LAST = true;
 
 // Largest r in [0, n) with S[r] <= w (S non-decreasing, S[0] <= w). The index
 // offsets are read-only during enumeration; the frontier prefix is rewritten
@@ -291,8 +294,11 @@ __device__ void expand_warps(const EnumArgs& A) {
     uint32_t probes = 0;  // a statistic (saturates per warp)
     for (uint64_t t = gwarp; t < total_tiles;) {
         cn.mark();
-        // the step's tiles: those of fusing slots first, then the others
-        const uint32_t* tb = t < __ldcg(A.tile_base + A.n_slots) ? A.tile_base : A.tile_base + A.n_slots + 1;
+        // the step's tiles: those of fusing slots first, then those of the other
+        // intermediate levels, then the last level's
+        const uint32_t* tb = A.tile_base;
+        if (t >= __ldcg(A.tile_base + A.n_slots)) tb += A.n_slots + 1;
+        if (t >= __ldcg(A.tile_base + 2 * A.n_slots + 1)) tb = A.tile_base + 2 * (A.n_slots + 1);
         const int s = (int)warp_find(tb, 0, (uint64_t)A.n_slots, t, lane);
         const SlotDesc* __restrict__ D = A.slots + s;
         SlotState* S = A.state + s;
@@ -877,13 +883,17 @@ __device__ void slot_start(const SlotDesc* D, SlotState* S) {
 template <int CT>
 __device__ void control_step(const EnumArgs& A, bool first) {
     using Scan = cub::BlockScan<unsigned long long, CT>;
+    using Scan32 = cub::BlockScan<uint32_t, CT>;
     __shared__ typename Scan::TempStorage tmp;
+    __shared__ typename Scan32::TempStorage tmp32;
     __shared__ unsigned long long carry_s;
+    __shared__ uint32_t carry_last_s;
     __shared__ int32_t active_s;
     __shared__ int32_t expired_s;
     __shared__ unsigned long long work_s;
     if (threadIdx.x == 0) {
         carry_s = 0;
+        carry_last_s = 0;
         active_s = 0;
         work_s = 0;
         // bound the whole enumeration in time: past the limit every slot stops
@@ -946,42 +956,59 @@ __device__ void control_step(const EnumArgs& A, bool first) {
     // A slot whose step makes the second-to-last level's partial matches also
     // expands most of their last level inside the same tiles (fused, up to
     // FUSE_FANOUT items per partial match): its tiles are cut smaller, so that
-    // no single tile holds the step's end, and are numbered before the step's
-    // other tiles, so that the heaviest are handed out first. tile_base holds
-    // two prefixes over the slots: [0, n] of the fusing slots' tiles (F in
-    // all), [n + 1, 2n + 1] of the others', from F on. One scan of both counts
-    // packed in 64 bits (each total is below 2^32).
+    // no single tile holds the step's end. The step's tiles are numbered
+    // heaviest first: the fusing slots', those of the other intermediate
+    // levels (which store partial matches), the last level's. tile_base holds
+    // three prefixes over the slots, each class from the end of the one before:
+    // [0, n] fusing (F tiles), [n + 1, 2n + 1] intermediate (M), [2n + 2, 3n + 2]
+    // last level. The first two counts are scanned packed in 64 bits (each total
+    // is below 2^32).
     const uint64_t tile_fused = max((uint64_t)32, (tile / FUSED_TILE_DIV) & ~(uint64_t)31);
-    for (int base = 0; base < A.n_slots; base += CT) {
+    const int n = A.n_slots;
+    for (int base = 0; base < n; base += CT) {
         const int s = base + threadIdx.x;
-        unsigned long long tiles = 0;  // fused << 32 | other
-        if (s < A.n_slots) {
+        unsigned long long fm = 0;  // fusing << 32 | intermediate
+        uint32_t nl = 0;             // last level
+        if (s < n) {
             SlotState* S = A.state + s;
             if (S->cur >= 0) {
                 const int k = A.slots[s].k;
                 const bool fused = k >= 3 && S->cur + 1 == k - 2;
+                const bool to_last = k == 1 || S->cur + 1 == k - 1;
                 const uint64_t ts = fused ? tile_fused : tile;
                 S->tile = (uint32_t)ts;
                 const uint64_t nt = (S->ce - S->cb + ts - 1) / ts;
-                tiles = fused ? nt << 32 : nt;
+                if (fused) fm = nt << 32;
+                else if (to_last && LAST_LEVEL_TILES_LAST) nl = (uint32_t)nt;
+                else fm = nt;
             }
         }
         unsigned long long excl, total;
-        Scan(tmp).ExclusiveSum(tiles, excl, total);
-        if (s < A.n_slots) {
+        Scan(tmp).ExclusiveSum(fm, excl, total);
+        uint32_t lexcl, ltotal;
+        Scan32(tmp32).ExclusiveSum(nl, lexcl, ltotal);
+        if (s < n) {
             A.tile_base[s] = (uint32_t)((carry_s + excl) >> 32);
-            A.tile_base[A.n_slots + 1 + s] = (uint32_t)(carry_s + excl);  // F added below
+            A.tile_base[n + 1 + s] = (uint32_t)(carry_s + excl);  // F added below
+            A.tile_base[2 * n + 2 + s] = carry_last_s + lexcl;   // F + M added below
         }
         __syncthreads();
-        if (threadIdx.x == 0) carry_s += total;
+        if (threadIdx.x == 0) {
+            carry_s += total;
+            carry_last_s += ltotal;
+        }
         __syncthreads();
     }
-    const uint32_t nfused = (uint32_t)(carry_s >> 32), nother = (uint32_t)carry_s;
-    for (int s = threadIdx.x; s < A.n_slots; s += CT) A.tile_base[A.n_slots + 1 + s] += nfused;
+    const uint32_t nfused = (uint32_t)(carry_s >> 32), nmid = (uint32_t)carry_s, nlast = carry_last_s;
+    for (int s = threadIdx.x; s < n; s += CT) {
+        A.tile_base[n + 1 + s] += nfused;
+        A.tile_base[2 * n + 2 + s] += nfused + nmid;
+    }
     if (threadIdx.x == 0) {
-        A.tile_base[A.n_slots] = nfused;
-        A.tile_base[2 * A.n_slots + 1] = nfused + nother;
-        A.sched->total_tiles = nfused + nother;
+        A.tile_base[n] = nfused;
+        A.tile_base[2 * n + 1] = nfused + nmid;
+        A.tile_base[3 * n + 2] = nfused + nmid + nlast;
+        A.sched->total_tiles = nfused + nmid + nlast;
         A.sched->tile = (uint32_t)tile;
         A.sched->tile_next = 0;
         A.sched->active = active_s;

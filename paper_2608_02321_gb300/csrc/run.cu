@@ -150,7 +150,7 @@ int tables_alloc(cudaMemPool_t pool, int max_slots, int block_threads, int tile_
     const size_t o_desc = L.take(sizeof(SlotDesc) * max_slots);
     const size_t o_state = L.take(sizeof(SlotState) * max_slots);
     const size_t o_sched = L.take(sizeof(Sched));
-    const size_t o_tiles = L.take(4ull * 2 * (max_slots + 1));  // two tile prefixes
+    const size_t o_tiles = L.take(4ull * 3 * (max_slots + 1));  // three tile prefixes
     const size_t o_err = L.take(4);
     const size_t zero_end = L.size;
     const size_t o_vptr = L.take(sizeof(int32_t*) * max_slots);
