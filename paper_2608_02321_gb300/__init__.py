@@ -10,7 +10,6 @@ from __future__ import annotations
 import ctypes as C
 import os
 import threading
-import weakref
 
 import numpy as np
 
@@ -295,16 +294,25 @@ class Graph:
         _check(lib.gfd_graph_load(C.byref(d), C.byref(o), C.byref(h)))
         del keep
         self._h = h
-        self._sessions = weakref.WeakSet()
+        # The graph's handle and those of its open sessions, shared with the
+        # sessions by strong reference. A session runs on the graph's stream
+        # and memory pool, so it must be freed first; when a graph and its
+        # sessions are garbage in one reference cycle, Python runs their
+        # finalisers in any order (and clears weak references before any of
+        # them), so whichever finaliser runs first frees the open sessions.
+        self._live = {"graph": h, "sessions": set()}
 
     def __del__(self):
-        if getattr(self, "_h", None) and _lib is not None:
-            # a session runs on the graph's stream: free it first (Python may
-            # finalise the two in either order when both are garbage at once)
-            for sess in list(getattr(self, "_sessions", ())):
-                sess.close()
-            _lib.gfd_graph_free(self._h)
-            self._h = None
+        live = getattr(self, "_live", None)
+        if live is None or _lib is None:
+            return
+        for sh in list(live["sessions"]):
+            _lib.gfd_session_free(C.c_void_p(sh))
+        live["sessions"].clear()
+        if live["graph"] is not None:
+            _lib.gfd_graph_free(live["graph"])
+            live["graph"] = None
+        self._h = None
 
     @property
     def device_bytes(self) -> int:
@@ -344,17 +352,21 @@ class Session:
 
     def __init__(self, g: Graph, max_slots: int = 64, **opts):
         self._g = g  # keeps the graph alive
+        self._live = g._live
         o = make_opts(**opts)
         h = C.c_void_p(None)
         _check(_lib.gfd_session_create(g._h, int(max_slots), C.byref(o), C.byref(h)))
         self._h = h
-        g._sessions.add(self)
+        self._live["sessions"].add(h.value)
 
     def close(self):
-        """Release the session (gfd_session_free); later calls are errors."""
-        if getattr(self, "_h", None) and _lib is not None:
-            _lib.gfd_session_free(self._h)
-            self._h = None
+        """Release the session (gfd_session_free); later calls are errors.
+        A no-op once its graph has been finalised (which freed it)."""
+        h, live = getattr(self, "_h", None), getattr(self, "_live", None)
+        if h and live is not None and _lib is not None and h.value in live["sessions"]:
+            live["sessions"].discard(h.value)
+            _lib.gfd_session_free(h)
+        self._h = None
 
     def __del__(self):
         self.close()
