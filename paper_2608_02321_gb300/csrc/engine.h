@@ -171,6 +171,10 @@ int variant_threads(int variant);
 constexpr int N_VARIANTS = 6;
 
 // ---- orchestration (run.cu)
+// SM count of the current device (queried once per device; 1 if the query
+// fails, and the next launch then reports the error).
+int device_sms();
+
 int graph_load(const gfd_graph_desc* d, const gfd_opts* o, gfd_graph** out);
 void graph_free(gfd_graph* g);
 void engine_free(Engine* e);

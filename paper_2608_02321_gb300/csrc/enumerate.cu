@@ -1224,7 +1224,7 @@ int init_slots(const EnumArgs& a, const int* host_ids, int n, cudaStream_t st) {
 
 int launch_split(const SlotDesc* slots, const int32_t* arena, uint64_t n, int32_t stride, int32_t* const* lists,
                  unsigned long long* cursor, cudaStream_t st) {
-    const int grid = (int)std::min<uint64_t>((n + 255) / 256, 152 * 16);
+    const int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)device_sms() * 16);
     k_split<<<std::max(grid, 1), 256, 0, st>>>(slots, arena, n, stride, lists, cursor);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GFD_OK : cuda_fail(e, "k_split");

@@ -9,6 +9,8 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -167,7 +169,7 @@ struct TmpFree {
 
 int grid_for(int64_t n, int threads = 256) {
     int64_t b = (n + threads - 1) / threads;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)device_sms() * 16));
 }
 
 std::string bad_text(uint32_t bad) {
@@ -181,6 +183,23 @@ std::string bad_text(uint32_t bad) {
 }
 
 }  // namespace
+
+int device_sms() {
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    const auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        return 1;  // not cached: a later call may succeed
+    }
+    cache.emplace(dev, sms);
+    return sms;
+}
 
 int graph_load(const gfd_graph_desc* d, const gfd_opts* o, gfd_graph** out) {
     if (!d || !out) {

@@ -748,17 +748,17 @@ int resident_grid(const void* fn, int threads) {
     static std::map<std::pair<const void*, int>, int> cache;
     int dev = 0;
     cudaGetDevice(&dev);
+    const int sms = device_sms();
     std::lock_guard<std::mutex> lk(mu);
     const auto key = std::make_pair(fn, dev);
     const auto it = cache.find(key);
     if (it != cache.end()) return it->second;
-    int sms = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();  // the launch itself reports a kernel that cannot run
         per_sm = 1;
     }
-    const int grid = std::max(1, sms) * per_sm;
+    const int grid = sms * per_sm;
     cache.emplace(key, grid);
     return grid;
 }
@@ -778,7 +778,7 @@ int check_launch(const char* what) {
 
 int launch_filter(const DevGraph& g, const FilterKey* d_keys, int nkeys, uint32_t* d_out, cudaStream_t st) {
     if (nkeys <= 0 || g.nwords == 0) return GFD_OK;
-    int blocks = (int)std::min<uint64_t>((g.nwords * 32 + FILTER_THREADS - 1) / FILTER_THREADS, 152 * 8);
+    int blocks = (int)std::min<uint64_t>((g.nwords * 32 + FILTER_THREADS - 1) / FILTER_THREADS, (uint64_t)device_sms() * 8);
     // keys staged in shared memory: at most KEYS_PER_LAUNCH per launch
     constexpr int KEYS_PER_LAUNCH = 4096;
     for (int k0 = 0; k0 < nkeys; k0 += KEYS_PER_LAUNCH) {
@@ -798,7 +798,7 @@ int launch_filter(const DevGraph& g, const FilterKey* d_keys, int nkeys, uint32_
 int launch_and(const DevGraph& g, const AndJob* d_jobs, int njobs, cudaStream_t st) {
     if (njobs <= 0 || g.nwords == 0) return GFD_OK;
     const uint32_t nch = (g.nwords + AND_WORDS - 1) / AND_WORDS;
-    const int grid = (int)std::min<uint64_t>((uint64_t)njobs * nch, 152 * 16);
+    const int grid = (int)std::min<uint64_t>((uint64_t)njobs * nch, (uint64_t)device_sms() * 16);
     k_and<<<grid, AND_THREADS, 0, st>>>(g, d_jobs, njobs, nch);
     return check_launch("k_and");
 }
@@ -810,7 +810,7 @@ uint32_t compact_chunks(const DevGraph& g) {
 int launch_compact(const DevGraph& g, const CompactJob* d_jobs, int njobs, cudaStream_t st) {
     if (njobs <= 0) return GFD_OK;
     const uint32_t nch = compact_chunks(g);
-    const int grid = (int)std::min<uint64_t>((uint64_t)njobs * nch, 152 * 8);
+    const int grid = (int)std::min<uint64_t>((uint64_t)njobs * nch, (uint64_t)device_sms() * 8);
     k_compact_sums<<<grid, COMPACT_THREADS, 0, st>>>(g, d_jobs, njobs, nch);
     k_compact_write<<<grid, COMPACT_THREADS, 0, st>>>(g, d_jobs, njobs, nch);
     return check_launch("k_compact");
@@ -853,7 +853,7 @@ int launch_cpi_count(const DevGraph& g, const CpiJob* d_jobs, int njobs, uint32_
     if (hq.scan) k_cpi_count<true><<<grid_of(k_cpi_count<true>, WARP_KERNEL_THREADS), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
     else k_cpi_count<false><<<grid_of(k_cpi_count<false>, WARP_KERNEL_THREADS), WARP_KERNEL_THREADS, 0, st>>>(g, d_jobs, njobs, hq);
     k_cpi_count_hub<<<grid_of(k_cpi_count_hub, HUB_THREADS), HUB_THREADS, 0, st>>>(g, d_jobs, hq);
-    const int grid = (int)std::min<uint64_t>((uint64_t)njobs * nchunks, 152 * 8);
+    const int grid = (int)std::min<uint64_t>((uint64_t)njobs * nchunks, (uint64_t)device_sms() * 8);
     k_cpi_sums<<<grid, COMPACT_THREADS, 0, st>>>(d_jobs, njobs, nchunks);
     k_cpi_scan<<<grid, COMPACT_THREADS, 0, st>>>(d_jobs, njobs, nchunks, d_err);
     k_cpi_totals<<<(njobs + 255) / 256, 256, 0, st>>>(d_jobs, njobs, d_totals);

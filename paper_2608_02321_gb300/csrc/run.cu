@@ -1487,7 +1487,7 @@ int result_sort_copy(gfd_result* r, int32_t* dst) {
     GFD_CUDA(cudaMallocAsync((void**)&k0, 8 * n, st));
     GFD_CUDA(cudaMallocAsync((void**)&k1, 8 * n, st));
     GFD_CUDA(cudaMallocAsync((void**)&sorted, 4 * n * k, st));
-    const int grid = (int)std::min<uint64_t>((n + 255) / 256, 152 * 16);
+    const int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)device_sms() * 16);
     k_iota<<<grid, 256, 0, st>>>(p0, n);
     size_t tb = 0;
     cub::DoubleBuffer<uint64_t> kb(k0, k1);
@@ -1571,7 +1571,7 @@ int results_sort_copy(gfd_result* const* rs, int n, int32_t* out, uint64_t capac
     GFD_CUDA(cudaMallocAsync((void**)&k1, 8 * total, st));
     GFD_CUDA(cudaMallocAsync((void**)&dout, 4 * ints, st));
     GFD_CUDA(cudaMemcpyAsync(d_src, src.data(), sizeof(PackSrc) * ((size_t)n + 1), cudaMemcpyHostToDevice, st));
-    const int grid = (int)std::min<uint64_t>((total + 255) / 256, 152 * 16);
+    const int grid = (int)std::min<uint64_t>((total + 255) / 256, (uint64_t)device_sms() * 16);
     k_pack_multi<<<grid, 256, 0, st>>>(d_src, n, total, W, M);
     k_iota<<<grid, 256, 0, st>>>(p0, total);
     size_t tb = 0;
