@@ -54,6 +54,10 @@ enum {
 #define GFD_ATTR_ABSENT INT32_MIN
 /* Largest pattern handled: |V_Q| <= GFD_MAX_K. */
 #define GFD_MAX_K 16
+/* Most GFDs one gfd_validate_batch (or gfd_autotune) call takes, and most slots
+ * of a session: every step of the enumeration numbers its work tiles in 32
+ * bits, and a slot's step holds up to 2^20 tiles. Split larger batches. */
+#define GFD_MAX_SLOTS 4095
 
 /*
  * Graph G = (V, E, L, F_A) (Section II, "directed labeled graphs with
@@ -219,7 +223,8 @@ int gfd_validate(const gfd_graph *g, const gfd_gfd *phi, const gfd_opts *opts,
 /* Validate n GFDs against the same resident graph in one batched run: the
  * candidate filters are shared between GFDs and all GFDs' matches are expanded
  * together by one persistent launch (Section II, Vio(Σ, G) as the per-GFD
- * lists). out[i] receives the result of phis[i]; on an error no entry is set. */
+ * lists). out[i] receives the result of phis[i]; on an error no entry is set.
+ * n above GFD_MAX_SLOTS gives GFD_ERR_UNSUPPORTED. */
 int gfd_validate_batch(const gfd_graph *g, const gfd_gfd *const *phis, int32_t n,
                        const gfd_opts *opts, gfd_result **out);
 
@@ -304,6 +309,8 @@ void gfd_result_free(gfd_result *r);
  * every request of the session (GFD_FLAG_NON_INDUCED, GFD_FLAG_PUSH_X);
  * disconnected patterns are admitted like any other.
  */
+/* max_slots: requests running at once, 1..GFD_MAX_SLOTS (else
+ * GFD_ERR_INVALID_ARG). */
 int gfd_session_create(const gfd_graph *g, int32_t max_slots, const gfd_opts *opts,
                        gfd_session **out);
 /* Queue one GFD (copied); *request_id identifies its result. The GFD is

@@ -26,6 +26,7 @@ GFD_ERR_CUDA = 6
 WILDCARD = -1
 ATTR_ABSENT = np.iinfo(np.int32).min
 MAX_K = 16
+MAX_SLOTS = 4095  # GFDs per batch call, running requests per session
 
 FLAG_NO_REFINE = 0x1
 FLAG_HOST_LOOP = 0x2

@@ -768,6 +768,11 @@ int run_batch(gfd_graph* g, const gfd_gfd* const* phis, int32_t n, const gfd_opt
         return GFD_ERR_INVALID_ARG;
     }
     if (n == 0) return GFD_OK;
+    if (n > GFD_MAX_SLOTS) {
+        set_error(GFD_ERR_UNSUPPORTED, "validate: %d GFDs in one call, at most %d (split the batch)", n,
+                  GFD_MAX_SLOTS);
+        return GFD_ERR_UNSUPPORTED;
+    }
     const int32_t flags = o ? o->flags : 0;
     const bool refine = !(flags & GFD_FLAG_NO_REFINE);
     const bool persistent = !(flags & GFD_FLAG_HOST_LOOP);
@@ -975,7 +980,7 @@ struct gfd_session {
 namespace gfd {
 
 int session_create(gfd_graph* g, int32_t max_slots, const gfd_opts* o, gfd_session** out) {
-    if (!g || !out || max_slots < 1 || max_slots > 4096) {
+    if (!g || !out || max_slots < 1 || max_slots > GFD_MAX_SLOTS) {
         set_error(GFD_ERR_INVALID_ARG, "gfd_session_create: bad argument");
         return GFD_ERR_INVALID_ARG;
     }

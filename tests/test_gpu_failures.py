@@ -84,6 +84,20 @@ def test_allocation_failure_is_reported(workload):
     _check_all(dg.validate_batch(qs), want, "after an allocation failure")
 
 
+def test_batch_over_the_slot_limit_is_refused(workload):
+    """A call over GFD_MAX_SLOTS GFDs is refused before any device work (its
+    steps would number their tiles past 32 bits); the graph stays usable."""
+    g, qs, want = workload
+    dg = gpu_graph(g)
+    with pytest.raises(G.GfdError) as e:
+        dg.validate_batch([qs[0]] * (G.MAX_SLOTS + 1))
+    assert e.value.code == G.GFD_ERR_UNSUPPORTED
+    with pytest.raises(G.GfdError) as e:
+        G.Session(dg, max_slots=G.MAX_SLOTS + 1)
+    assert e.value.code == G.GFD_ERR_INVALID_ARG
+    _check_all(dg.validate_batch(qs), want, "after a refused batch")
+
+
 def _drain(s, limit=100000):
     out = {}
     for _ in range(limit):
