@@ -410,8 +410,7 @@ def main():
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
     # e2e: host GFDs in, sorted violation tuples back on the host (one untimed
-    # warm-up call first: it allocates the pinned host block that later calls
-    # reuse)
+    # warm-up call first)
     G.violations_all(step())
     e2e_times = []
     d2h = 0
