@@ -397,7 +397,7 @@ def main():
                 "frac": achieved / peak if peak else None, "traffic": traffic,
                 "traffic_source": "ncu DRAM bytes per work item of a small capture x this launch's work items",
                 "kernel": "k_persistent (enumeration)", "launch_ms": t_enum * 1000,
-                "model": "algorithmic bytes of the survey's byte model (index reads 4 B per N_u entry, "
+                "model": "algorithmic bytes (index reads 4 B per N_u entry, "
                          "backward non-tree adjacency 5 B per entry, 32 B per binary-search step of an absent-edge "
                          "probe, 32 B per literal attribute read, 4k B per violation), counted by an untimed "
                          "counting pass of the same launch",
