@@ -195,7 +195,10 @@ int gfd_graph_load(const gfd_graph_desc *desc, const gfd_opts *opts, gfd_graph *
 
 /* Release a graph handle and its device memory (the graph G of Section II
  * loaded by gfd_graph_load). Waits for work still running on the graph's
- * stream; NULL is a no-op. */
+ * stream; NULL is a no-op. Free the graph's sessions first. Its results stay
+ * valid for their counts, for tuples already read to the host and for
+ * gfd_result_free, but tuples not yet read are sorted on the graph's stream
+ * (unless the call named another): read them before freeing the graph. */
 void gfd_graph_free(gfd_graph *g);
 
 /* Autotuner: validate the batch phis[0..n) once per enumeration-kernel variant,

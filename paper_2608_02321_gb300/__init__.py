@@ -207,8 +207,11 @@ class _GfdBuf:
 class Result:
     """Matches and violations of one GFD."""
 
-    def __init__(self, handle):
+    def __init__(self, handle, graph=None):
         self._h = handle
+        # the tuples are sorted on the graph's stream when first read: the
+        # graph stays loaded while its results are reachable
+        self._g = graph
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -324,7 +327,7 @@ class Graph:
         b = _GfdBuf(gfd)
         h = C.c_void_p(None)
         _check(_lib.gfd_validate(self._h, C.byref(b.s), C.byref(o), C.byref(h)))
-        return Result(h)
+        return Result(h, self)
 
     def autotune(self, gfds, **opts) -> dict:
         """Time the enumeration-kernel variants and frontier budgets on this
@@ -343,7 +346,7 @@ class Graph:
         arr = (C.POINTER(gfd_gfd) * max(1, len(bufs)))(*[C.pointer(b.s) for b in bufs])
         outs = (C.c_void_p * max(1, len(bufs)))()
         _check(_lib.gfd_validate_batch(self._h, arr, len(bufs), C.byref(o), outs))
-        return [Result(C.c_void_p(outs[i])) for i in range(len(bufs))]
+        return [Result(C.c_void_p(outs[i]), self) for i in range(len(bufs))]
 
 
 class Session:
@@ -407,7 +410,7 @@ class Session:
             _check(_lib.gfd_session_next_result(self._h, C.byref(rid), C.byref(h)))
             if rid.value < 0:
                 return out
-            out.append((int(rid.value), Result(h)))
+            out.append((int(rid.value), Result(h, self._g)))
 
 
 def node_candidates_noalloc(g: Graph, gfd, node: int, out_ptr: int, out_cap: int, stream=None) -> int:

@@ -123,3 +123,30 @@ def test_reference_cycle_collected(fake):
             freed_graphs.add(h)
         else:
             assert owner[h] not in freed_graphs, "a session was freed after its graph"
+
+
+def test_results_keep_their_graph(fake, monkeypatch):
+    """A result's tuples are sorted on its graph's stream when first read, so
+    the graph is released only after its last result."""
+    from synth.gfds import GFD
+
+    def validate(g, phi, opts, out):
+        fake.calls.append(("validate", fake._new(out)))
+        return G.GFD_OK
+
+    def result_free(h):
+        fake.calls.append(("result_free", h.value if isinstance(h, C.c_void_p) else h))
+
+    monkeypatch.setattr(fake, "gfd_validate", validate, raising=False)
+    monkeypatch.setattr(fake, "gfd_result_free", result_free, raising=False)
+    g = G.Graph(_TinyGraph())
+    g_h = g._h.value
+    r = g.validate(GFD([0, 0], [(0, 1, -1)], [], [], True, "edge"))
+    r_h = r._h.value
+    del g
+    gc.collect()
+    assert not any(k == "graph_free" for k, _ in fake.calls), "graph freed while a result is alive"
+    del r
+    gc.collect()
+    frees = [c for c in fake.calls if c[0] in ("result_free", "graph_free")]
+    assert frees == [("result_free", r_h), ("graph_free", g_h)]
